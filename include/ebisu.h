@@ -1,0 +1,313 @@
+/*
+ * ebisu.h -- C ABI of the GB300 temporally blocked stencil library.
+ *
+ * The library runs many Jacobi time steps of a fixed-coefficient star or box
+ * stencil on one GPU.  The update it computes is the one of Section 2.1 of
+ * "Revisiting Temporal Blocking Stencil Optimizations" (ICS '23; Listings 1-3,
+ * benchmark shapes of Table 2):
+ *
+ *     u_s(x) = sum_k c_k * u_{s-1}(x + o_k),   s = 1 .. steps,
+ *
+ * over every interior cell x, with the offsets o_k taken in canonical order
+ * (lexicographic in (dz, dy, dx)) and the sum taken as
+ *     acc = c_0 * u(o_0);  acc = fma(c_k, u(o_k), acc) for k = 1 .. P-1.
+ * Temporal blocking (Sections 3-4: tile-by-tile execution, circular
+ * multi-queue, lazy streaming) reorders these updates without changing them,
+ * so the blocked path returns bit-for-bit what the one-step-per-launch path
+ * (ebisu_run_naive) returns.
+ *
+ * Conventions shared by every entry point
+ *   - Layout: row-major, x fastest.  2D grids are (ny, nx), 3D grids
+ *     (nz, ny, nx); `dims` always lists interior extents slowest first.
+ *   - Dirichlet grids are stored padded by `radius` cells on every side,
+ *     (n + 2r) per axis; the pad holds fixed values that are read and never
+ *     changed.  Periodic grids are stored unpadded, n per axis; neighbours
+ *     wrap modulo n.
+ *   - Storage types: EBISU_F64 (double), EBISU_F32 (float), EBISU_BF16
+ *     (bfloat16, 2 bytes).  F64 computes in double.  F32 and BF16 compute in
+ *     float with the coefficients rounded to float, and round every step's
+ *     result to the storage type (round to nearest even), including the
+ *     intermediate steps inside a temporal block.
+ *   - Memory: every pointer to grid data or workspace is a device pointer
+ *     owned by the caller (unless a function says host pointer).  Plans own
+ *     host memory only.  `stream` is a cudaStream_t (NULL = legacy default
+ *     stream); work is enqueued asynchronously on it.
+ *   - Errors: argument errors are returned synchronously and nothing is
+ *     enqueued.  Errors found by the kernels (a dependency wait that ran out
+ *     of time, a failed launch) are reported by ebisu_sync(), which waits
+ *     for the stream and reads the status word in the workspace.
+ */
+#ifndef EBISU_H
+#define EBISU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ebisu_plan_s* ebisu_plan_t;
+typedef struct ebisu_batch_s* ebisu_batch_t;
+typedef struct ebisu_server_s* ebisu_server_t;
+
+enum ebisu_status {
+    EBISU_OK = 0,
+    EBISU_ERR_INVALID_ARG = 1,  /* a null pointer, a bad enum or size        */
+    EBISU_ERR_UNSUPPORTED = 2,  /* radius/shape/size outside what is built    */
+    EBISU_ERR_CUDA = 3,         /* a CUDA runtime call failed                 */
+    EBISU_ERR_OOM = 4,          /* a host allocation failed                   */
+    EBISU_ERR_BUDGET = 5,       /* serving: request exceeds the HBM budget    */
+    EBISU_ERR_TIMEOUT = 6,      /* a device-side wait gave up (bounded spin)  */
+    EBISU_ERR_DEVICE_FAULT = 7, /* a kernel reported an inconsistent state    */
+    EBISU_ERR_NOT_READY = 8,    /* serving: the request has not finished      */
+    EBISU_ERR_BUSY = 9          /* serving: queue full, request rejected      */
+};
+
+enum ebisu_shape { EBISU_STAR = 0, EBISU_BOX = 1 };
+enum ebisu_dtype { EBISU_F64 = 0, EBISU_F32 = 1, EBISU_BF16 = 2 };
+enum ebisu_boundary { EBISU_DIRICHLET = 0, EBISU_PERIODIC = 1 };
+
+/* Execution parameters of a plan (the tuner's search space, Sections 5-6):
+ *   tile_x, tile_y : output tile extents in x and (3D only) y; the tile is
+ *                    streamed along the slowest axis (y in 2D, z in 3D),
+ *                    Section 2.1.3 / 3.
+ *   tile_s         : length of the streamed band along the slowest axis
+ *                    (0 = the whole axis).
+ *   depth          : temporal block depth t (steps fused per pass, >= 1).
+ *   ctas_per_sm    : resident CTAs per SM (the paper's minimal parallelism,
+ *                    Section 6.1, is one 256-thread CTA per SM).
+ *   threads        : threads per CTA (multiple of 32, <= 1024).
+ *   variant        : 0 = temporally blocked persistent kernel, 1 = naive
+ *                    one-step-per-launch kernel. */
+typedef struct ebisu_params {
+    int32_t tile_x;
+    int32_t tile_y;
+    int32_t tile_s;
+    int32_t depth;
+    int32_t ctas_per_sm;
+    int32_t threads;
+    int32_t variant;
+    int32_t reserved;
+} ebisu_params;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* ebisu_status_string(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int ebisu_version(void);
+
+/* Create a plan (host only; no device memory is touched).
+ *   ndim      : 2 or 3.
+ *   dims      : host array of ndim interior extents, slowest first, each >= 1
+ *               (periodic: each >= 2*radius+1).
+ *   shape     : EBISU_STAR (centre + axis offsets |k| <= r) or EBISU_BOX
+ *               (all offsets with max |k| <= r); Table 2 of the paper.
+ *   radius    : 1..3 for star, 1..2 for box.
+ *   coeffs    : host array of P weights in canonical offset order
+ *               (P = 2*ndim*r+1 for star, (2r+1)^ndim for box); copied.
+ *   dtype     : storage type (enum ebisu_dtype).
+ *   boundary  : EBISU_DIRICHLET (padded, fixed pad) or EBISU_PERIODIC.
+ *   out       : receives the plan.
+ * The execution parameters start at the cost model's choice (Section 5-6);
+ * ebisu_plan_set_params or ebisu_plan_tune may replace them. */
+int ebisu_plan_create(int ndim, const int64_t* dims, int shape, int radius,
+                      const double* coeffs, int dtype, int boundary,
+                      ebisu_plan_t* out);
+
+/* Destroy a plan.  Plans may be destroyed while work that used them is still
+ * in flight: launches copy what they need. */
+int ebisu_plan_destroy(ebisu_plan_t plan);
+
+/* Number of support points P of the plan's stencil. */
+int ebisu_plan_npoints(ebisu_plan_t plan, int* npts);
+
+/* Stored element count of the plan's grid (padded extents multiplied). */
+int ebisu_plan_grid_elems(ebisu_plan_t plan, int64_t* elems);
+
+/* Read or replace the execution parameters.  set_params validates them
+ * against the device (shared memory, co-residency) and returns
+ * EBISU_ERR_UNSUPPORTED if they cannot run. */
+int ebisu_plan_get_params(ebisu_plan_t plan, ebisu_params* p);
+int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* p);
+
+/* Bytes of device workspace a run of this plan needs: a control block plus
+ * one grid-sized ping-pong buffer (the paper's two time levels, Listing 4). */
+int ebisu_plan_workspace_bytes(ebisu_plan_t plan, size_t* bytes);
+
+/* Run `steps` time steps: out = S^steps(in), temporally blocked.
+ *   in        : device grid, read only (unless in == out).
+ *   out       : device grid of the same stored shape; its Dirichlet pad is
+ *               copied from `in`.  in == out is allowed.
+ *   steps     : >= 0; 0 copies in to out.
+ *   workspace : device memory of ebisu_plan_workspace_bytes bytes, 256-byte
+ *               aligned; must not be used by another call that overlaps on
+ *               the GPU.
+ *   stream    : cudaStream_t.
+ * Enqueues work and returns; call ebisu_sync for device-side errors. */
+int ebisu_run(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
+              void* workspace, void* stream);
+
+/* The same result through the naive path: one kernel launch per time step,
+ * each thread reading its neighbours straight from global memory, with the
+ * same per-cell summation order.  This is the reference GPU path that the
+ * blocked kernel must equal bit for bit. */
+int ebisu_run_naive(ebisu_plan_t plan, const void* in, void* out,
+                    int64_t steps, void* workspace, void* stream);
+
+/* Wait for `stream`, then read and clear the status word that kernels of
+ * the last run on `workspace` left there.  Returns EBISU_OK, EBISU_ERR_CUDA
+ * (a CUDA error, whose text ebisu_last_cuda_error gives) or the kernel's
+ * status (EBISU_ERR_TIMEOUT, EBISU_ERR_DEVICE_FAULT). */
+int ebisu_sync(void* workspace, void* stream);
+
+/* Text of the last CUDA error seen by this thread (static or thread-local
+ * storage, never NULL). */
+const char* ebisu_last_cuda_error(void);
+
+/* Empirical autotuning (Sections 6.3-6.4: the cost model prunes, the
+ * measurement decides).  Times up to `max_candidates` parameter sets from the
+ * cost model's ranking on the caller's buffers (in is not modified; out and
+ * workspace are overwritten) for `steps` steps each, keeps the fastest in
+ * the plan and, if `best_ms` is not NULL, stores its time there.
+ * Synchronises the stream. */
+int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out,
+                    int64_t steps, void* workspace, int max_candidates,
+                    double* best_ms, void* stream);
+
+/* Cost model of Section 5 for the plan's current parameters on this
+ * device.  All outputs are optional (NULL to skip):
+ *   pred_cells_per_s : practical attainable performance PP = P x V.
+ *   bound            : 0 = global memory, 1 = shared memory, 2 = FP pipe.
+ *   valid_fraction   : V, the useful share of the computed cells. */
+int ebisu_plan_model(ebisu_plan_t plan, double* pred_cells_per_s, int* bound,
+                     double* valid_fraction);
+
+/* The paper's practical-attainable-performance model (Section 5) evaluated on
+ * caller-supplied machine and kernel figures (host only; the tuner uses the
+ * same code with this device's measured figures).
+ *   Eq. 2-5:  T_gm = a_gm D_gm S / B_gm,  T_sm = a_sm D_sm t S / B_sm,
+ *             T_cmp = a_cmp D_cmp t / THR_cmp;  T_stencil = max of the three.
+ *   Eq. 7:    P = D_all t / T_stencil  (D_all = d_cmp).
+ *   Eq. 8-9:  V_SMtile = prod over the (ndim-1) tiled axes of
+ *             (tile - 2 rad (t-1)) / tile  -- the tile is the region computed
+ *             in the first fused step; each further step loses rad per side.
+ *   Eq. 11:   V_Dtile = T_stencil / (T_stencil + T_Dsync n).
+ *   Eq. 1:    PP = P V (V per `tiling`).
+ *   Eq. 17:   desired depth, SM tiling: t >= a_gm D_gm B_sm / (a_sm D_sm B_gm).
+ *   Eq. 18-19: desired depth, device tiling with
+ *             D_gm = tx ty + (tx + ty) 2 t rad, D_sm = tx ty.
+ *   Eq. 23:   smallest square device-tile side 4 a_gm B_sm rad / (a_sm B_gm).
+ * Every input is a plain number (units: cells, bytes, bytes/s, flop/s, s). */
+typedef struct ebisu_model_in {
+    double a_gm, a_sm, a_cmp;    /* accesses (or flops) per cell             */
+    double d_gm, d_sm, d_cmp;    /* cells moved / cached / computed          */
+    double s_cell;               /* bytes per cell                           */
+    double b_gm, b_sm, thr_cmp;  /* bandwidths (B/s), FP throughput (flop/s) */
+    double t;                    /* temporal depth                           */
+    double t_dsync, n_sync;      /* device-wide sync cost (s), syncs per tile */
+    double tile_x, tile_y, rad;  /* SM tile (first-step region) and radius   */
+    int32_t ndim;                /* 2 or 3                                   */
+    int32_t tiling;              /* 0 = SM tiling, 1 = device tiling         */
+} ebisu_model_in;
+
+typedef struct ebisu_model_out {
+    double t_gm, t_sm, t_cmp, t_stencil; /* seconds                          */
+    double p;                            /* attainable cells/s (Eq. 7)       */
+    double v_smtile, v_dtile;            /* valid proportions (Eq. 8-11)     */
+    double pp;                           /* practical attainable (Eq. 1)     */
+    double depth_sm, depth_device;       /* desired depth (Eq. 17, 18-19)    */
+    double min_device_tile;              /* Eq. 23                           */
+    int32_t bound;                       /* 0 gm, 1 sm, 2 compute            */
+    int32_t reserved;
+} ebisu_model_out;
+
+int ebisu_cost_model(const ebisu_model_in* in, ebisu_model_out* out);
+
+/* FP64 reductions over the interior of a device grid (plan's layout and
+ * storage type; values are widened to double):
+ *   result[0] = sum, result[1] = L2 norm, result[2] = max |value|,
+ * of `a`, or of (a - b) when b is not NULL.  `result` is a HOST array of 3
+ * doubles.  Uses a fixed-order tree, so the result does not depend on the
+ * launch.  Synchronises the stream. */
+int ebisu_reduce(ebisu_plan_t plan, const void* a, const void* b,
+                 double* result, void* workspace, void* stream);
+
+/* Batched runs: n independent problems in one persistent launch per group
+ * of plans that share (ndim, shape, radius, dtype); the boundary, sizes,
+ * coefficients and parameters may differ.  The work table interleaves the
+ * problems' temporal blocks, so items of one problem fill the dependency
+ * waits of another.  Each result equals ebisu_run of the same problem alone,
+ * bit for bit.
+ *   plans, in, out, steps : host arrays of n entries (in/out hold device
+ *                           pointers; in[i] == out[i] is allowed).
+ *   workspace             : device memory of ebisu_batch_workspace_bytes
+ *                           bytes, 256-byte aligned.
+ * ebisu_batch_run = create + launch + destroy.  To replay a batch cheaply,
+ * ebisu_batch_create uploads the work tables into the workspace once
+ * (synchronising the stream); ebisu_batch_launch then enqueues only stream
+ * operations (a memset, device copies, kernel launches) and may be captured
+ * into a CUDA graph; ebisu_batch_sync waits and returns the first kernel
+ * status; ebisu_batch_destroy frees the host handle (any time after create).
+ * The plans are copied at create time. */
+int ebisu_batch_workspace_bytes(int n, const ebisu_plan_t* plans,
+                                const int64_t* steps, size_t* bytes);
+int ebisu_batch_run(int n, const ebisu_plan_t* plans, const void* const* in,
+                    void* const* out, const int64_t* steps, void* workspace,
+                    void* stream);
+int ebisu_batch_create(int n, const ebisu_plan_t* plans, const void* const* in,
+                       void* const* out, const int64_t* steps, void* workspace,
+                       void* stream, ebisu_batch_t* batch);
+int ebisu_batch_launch(ebisu_batch_t batch, void* stream);
+int ebisu_batch_sync(ebisu_batch_t batch, void* stream);
+int ebisu_batch_destroy(ebisu_batch_t batch);
+
+/* Serving loop (continuous batching, host thread + CUDA streams).
+ *   hbm_budget : bytes of device memory the server may hold for grids and
+ *                workspaces; requests are admitted while they fit.
+ *   max_slots  : requests that may run on the device at once.
+ * The server allocates and frees its own device memory inside the budget. */
+int ebisu_serve_create(size_t hbm_budget, int max_slots, ebisu_server_t* out);
+
+/* Submit a request: copy `in_dev` (device grid laid out as the plan says)
+ * into a resident buffer, run `steps` steps when admitted, and write the
+ * result to `out_dev`.  `in_dev` may be reused once ebisu_serve_poll reports
+ * the request done.  The plan is copied.  Returns EBISU_ERR_BUDGET if the
+ * request alone exceeds the budget and EBISU_ERR_BUSY if the queue already
+ * holds 1024 waiting requests (admission control: the request is dropped).
+ * *ticket receives the request id. */
+int ebisu_serve_submit(ebisu_server_t s, ebisu_plan_t plan, const void* in_dev,
+                       void* out_dev, int64_t steps, uint64_t* ticket);
+
+/* Non-blocking status of a request: *done = 1 once out_dev holds the
+ * result; *latency_s = seconds from submit to completion (or so far). */
+int ebisu_serve_poll(ebisu_server_t s, uint64_t ticket, int* done,
+                     double* latency_s);
+
+/* Block until the request finishes (or timeout_s passes: EBISU_ERR_NOT_READY). */
+int ebisu_serve_wait(ebisu_server_t s, uint64_t ticket, double timeout_s,
+                     double* latency_s);
+
+/* Counters: stats[0] submitted, [1] completed, [2] rejected, [3] queued now,
+ * [4] running now, [5] peak bytes held, [6] bytes held now. */
+int ebisu_serve_stats(ebisu_server_t s, int64_t* stats);
+
+/* Cancel a request that has not started (EBISU_ERR_NOT_READY if it has). */
+int ebisu_serve_cancel(ebisu_server_t s, uint64_t ticket);
+
+/* Drain all requests, stop the thread, free device memory. */
+int ebisu_serve_destroy(ebisu_server_t s);
+
+/* Device microbenchmarks that fill the roofline and the cost model
+ * (Section 6.1: Little's law needs measured throughputs).  All outputs are
+ * HOST pointers, each optional:
+ *   out[0] FP64 FMA rate (flop/s, 2 per FMA), out[1] FP32 FMA rate,
+ *   out[2] shared-memory load bandwidth (byte/s), out[3] device-wide
+ *   barrier latency (seconds), out[4] SM count, out[5] SM clock seen (Hz).
+ * Synchronises the device. */
+int ebisu_probe_device(double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EBISU_H */

@@ -1,0 +1,63 @@
+// common.h -- structures shared by the host orchestration and the kernels.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+namespace ebisu {
+
+constexpr int kMaxPoints = 125;        // 3D box of radius 2
+constexpr size_t kControlBytes = 4096; // status word, counters (single run)
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Control block at the start of every workspace.  Zeroed before each run.
+struct Control {
+    int status;          // 0 = ok, else an ebisu_status code set by a kernel
+    unsigned next_item;  // work-queue head (persistent kernels pop items)
+    unsigned wait_where; // diagnostic: item index of the wait that gave up
+    unsigned pad_[5];
+    unsigned done[1];    // per-problem completed-tile counters (ngrids)
+};
+
+// One problem of a (possibly batched) temporally blocked launch, in
+// streaming coordinates: s = slowest axis (y in 2D, z in 3D), p1 = y in 3D
+// (dummy, extent 1, in 2D), p2 = x.
+struct GridDesc {
+    const void* src0;    // input of the first temporal block
+    void* out;           // final destination
+    void* ws;            // ping-pong buffer
+    void* halo_dst0;     // buffers whose Dirichlet pad is filled from src0
+    void* halo_dst1;     //   during the first temporal block (or null)
+    int64_t n[3];        // interior extents (s, p1, p2)
+    int64_t lds;         // element stride between consecutive s
+    int64_t ld1;         // element stride between consecutive p1
+    int32_t pad;         // Dirichlet pad width (= radius), 0 if periodic
+    int32_t periodic;
+    int32_t tile[3];     // output tile extents (s, p1, p2)
+    int32_t nt[3];       // tiles per axis (s, p1, p2)
+    int32_t ntiles;
+    int32_t depth;       // temporal block depth t
+    int32_t nblocks;     // ceil(steps / depth)
+    int32_t last_depth;  // depth of the last block
+    int32_t grid_id;     // index into Control::done
+    int32_t load_mode;   // 0 = element cp.async, 1 = pair cp.async (2-byte
+                         // types, rows of a plane share parity), 2 = staged
+    int64_t total_elems; // stored elements of the grid (bounds of pair loads)
+    double coef[kMaxPoints];
+};
+
+// Kernel parameters of a temporally blocked launch.
+struct TBParams {
+    GridDesc g;                 // the problem, when `grids` is null
+    const GridDesc* grids;      // batched: per-problem descriptors (device)
+    const int32_t* items;       // batched: (grid, block, tile) triples (device)
+    int64_t nitems;
+    Control* ctl;
+    int64_t timeout_ns;         // bound on every dependency wait
+    int32_t debug_stall;        // test hook: 1 = the first wait targets a
+                                // count that is never reached
+    int32_t smem_plane;         // elements per ring plane
+};
+
+}  // namespace ebisu

@@ -1,0 +1,46 @@
+// dispatch.h -- host-callable launchers of the CUDA kernels, one set per
+// storage type (defined in kern_f64.cu, kern_f32.cu, kern_bf16.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.h"
+
+namespace ebisu {
+
+// Arguments of the naive one-step kernel (streaming coordinates, see GridDesc).
+struct NaiveParams {
+    int64_t n[3];
+    int64_t lds, ld1;
+    int32_t pad;
+    int32_t periodic;
+    double coef[kMaxPoints];
+};
+
+// Geometry of a stored grid for pad copies and reductions.
+struct PadParams {
+    int64_t n[3];     // interior extents (s, p1, p2)
+    int64_t lds, ld1; // element strides
+    int32_t pad;      // pad along s and p2
+    int32_t pad1;     // pad along p1 (0 in 2D)
+};
+
+#define EBISU_DECLARE_DTYPE_ENTRY(NAME)                                                          \
+    cudaError_t tb_launch_##NAME(int d, int s, int r, const TBParams& p, int g, size_t sm,       \
+                                 cudaStream_t st);                                               \
+    cudaError_t tb_occupancy_##NAME(int d, int s, int r, size_t sm, int* b);                     \
+    cudaError_t naive_launch_##NAME(int d, int s, int r, const void* a, void* b,                 \
+                                    const NaiveParams& p, cudaStream_t st);                      \
+    cudaError_t pad_copy_##NAME(const void* s, void* d0, void* d1, const PadParams& p,           \
+                                cudaStream_t st);                                                \
+    cudaError_t reduce_partial_##NAME(const void* a, const void* b, double* part,                \
+                                      const PadParams& p, int64_t* n, cudaStream_t st);
+
+EBISU_DECLARE_DTYPE_ENTRY(f64)
+EBISU_DECLARE_DTYPE_ENTRY(f32)
+EBISU_DECLARE_DTYPE_ENTRY(bf16)
+
+// util.cu
+cudaError_t reduce_final(const double* part, int64_t nparts, double* out3_dev, cudaStream_t st);
+cudaError_t probe_device(double* out6);
+
+}  // namespace ebisu

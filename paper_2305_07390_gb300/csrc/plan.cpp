@@ -1,0 +1,502 @@
+// plan.cpp -- plans, runs and the core of the C ABI (include/ebisu.h).
+#include "plan.h"
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+using namespace ebisu;
+
+namespace ebisu {
+
+static thread_local char g_err[512] = "no CUDA error";
+
+void set_cuda_error(cudaError_t e)
+{
+    snprintf(g_err, sizeof(g_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+int fail_cuda(cudaError_t e)
+{
+    set_cuda_error(e);
+    return EBISU_ERR_CUDA;
+}
+
+static std::mutex g_dev_mu;
+static DeviceInfo g_dev[16];
+
+const DeviceInfo& device_info()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) dev = 0;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DeviceInfo& d = g_dev[dev];
+    if (d.device < 0) {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+            d.sms = prop.multiProcessorCount;
+            d.smem_optin = prop.sharedMemPerBlockOptin;
+            d.smem_per_sm = prop.sharedMemPerMultiprocessor;
+            strncpy(d.name, prop.name, sizeof(d.name) - 1);
+        } else {
+            cudaGetLastError();
+            // no device: GB300 figures, so that plans can be built on a host
+            d.sms = 152;
+            d.smem_optin = 232448;
+            d.smem_per_sm = 233472;
+            strncpy(d.name, "no device", sizeof(d.name) - 1);
+        }
+        d.device = dev;
+    }
+    return d;
+}
+
+int64_t wait_timeout_ns()
+{
+    const char* e = getenv("EBISU_WAIT_TIMEOUT_MS");
+    if (e && *e) {
+        const long long ms = atoll(e);
+        if (ms > 0) return (int64_t)ms * 1000000LL;
+    }
+    return 60LL * 1000000000LL;
+}
+
+int ring_q(int radius) { return 2 * radius + 2; }
+int ring_q0(int radius) { return 2 * radius + 1 + kPrefetch; }
+
+// largest level-0 region of any tile: (E1, E2), unpadded
+static void max_plane(const ebisu_plan_s* p, const ebisu_params& q, int64_t* e1, int64_t* e2)
+{
+    const int r = p->radius;
+    const bool per = p->boundary == EBISU_PERIODIC;
+    const int64_t tx = std::min<int64_t>(q.tile_x, p->n[2]);
+    *e2 = tx + 2LL * r * q.depth;
+    if (!per) *e2 = std::min<int64_t>(*e2, p->n[2] + 2LL * p->pad);
+    *e1 = 1;
+    if (p->ndim == 3) {
+        const int64_t ty = std::min<int64_t>(q.tile_y, p->n[1]);
+        *e1 = ty + 2LL * r * q.depth;
+        if (!per) *e1 = std::min<int64_t>(*e1, p->n[1] + 2LL * p->pad);
+    }
+}
+
+int64_t plane_capacity(const ebisu_plan_s* p, const ebisu_params& q)
+{
+    int64_t e1, e2;
+    max_plane(p, q, &e1, &e2);
+    // row pitch: even and >= E2 + 2 (room for the pair-load shift)
+    const int64_t pitch = (e2 + 3) & ~(int64_t)1;
+    return e1 * pitch;
+}
+
+size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q)
+{
+    const size_t slots = (size_t)ring_q0(p->radius) + (size_t)(q.depth - 1) * ring_q(p->radius);
+    return slots * (size_t)plane_capacity(p, q) * p->esize;
+}
+
+int check_params(const ebisu_plan_s* p, const ebisu_params& q)
+{
+    if (q.variant != 0 && q.variant != 1) return EBISU_ERR_INVALID_ARG;
+    if (q.variant == 1) return EBISU_OK;
+    if (q.depth < 1 || q.depth > 64 || q.tile_x < 1 || (p->ndim == 3 && q.tile_y < 1) || q.tile_s < 0 ||
+        q.ctas_per_sm < 1 || q.ctas_per_sm > 8)
+        return EBISU_ERR_INVALID_ARG;
+    int64_t e1, e2;
+    max_plane(p, q, &e1, &e2);
+    if (e1 * e2 > (int64_t)kStagePerThread * kThreads) return EBISU_ERR_UNSUPPORTED;
+    const DeviceInfo& d = device_info();
+    if (tb_smem_bytes(p, q) + 4096 > d.smem_optin) return EBISU_ERR_UNSUPPORTED;
+    return EBISU_OK;
+}
+
+int64_t fill_grid_desc(const ebisu_plan_s* p, const void* in, void* out, void* wsgrid, int64_t steps,
+                       bool in_copied_to_ws, GridDesc* g)
+{
+    memset(g, 0, sizeof(*g));
+    const ebisu_params& q = p->prm;
+    const int d = (int)std::min<int64_t>(q.depth, std::max<int64_t>(steps, 1));
+    const int64_t nb = (steps + d - 1) / d;
+    g->src0 = in_copied_to_ws ? wsgrid : in;
+    g->out = out;
+    g->ws = wsgrid;
+    for (int i = 0; i < 3; ++i) g->n[i] = p->n[i];
+    g->lds = p->lds;
+    g->ld1 = p->ld1;
+    g->pad = p->pad;
+    g->periodic = p->boundary == EBISU_PERIODIC;
+    g->tile[2] = (int32_t)std::min<int64_t>(q.tile_x, p->n[2]);
+    g->tile[1] = (p->ndim == 3) ? (int32_t)std::min<int64_t>(q.tile_y, p->n[1]) : 1;
+    g->tile[0] = (q.tile_s <= 0) ? (int32_t)p->n[0] : (int32_t)std::min<int64_t>(q.tile_s, p->n[0]);
+    for (int i = 0; i < 3; ++i) g->nt[i] = (int32_t)((p->n[i] + g->tile[i] - 1) / g->tile[i]);
+    g->ntiles = g->nt[0] * g->nt[1] * g->nt[2];
+    g->depth = d;
+    g->nblocks = (int32_t)nb;
+    g->last_depth = (int32_t)(steps - (nb - 1) * d);
+    g->grid_id = 0;
+    g->total_elems = p->elems;
+    if (p->esize >= 4) {
+        g->load_mode = 0;  // one cp.async per element
+    } else {
+        // 2-byte elements: aligned 4-byte pairs when every row of a plane
+        // starts on the same parity and no row wraps, else staged loads
+        const bool rows_agree = (p->ndim == 2) || ((p->ld1 % 2 == 0) && (p->lds % 2 == 0));
+        const bool aligned = ((uintptr_t)in % 4 == 0) && ((uintptr_t)out % 4 == 0) &&
+                             ((uintptr_t)wsgrid % 4 == 0);
+        g->load_mode = (!g->periodic && rows_agree && aligned) ? 1 : 2;
+    }
+    for (int k = 0; k < p->npts; ++k) g->coef[k] = p->coef[k];
+    // Buffers whose Dirichlet pad must be filled during the first block.
+    void* dst0 = ((nb - 1) % 2 == 0) ? out : wsgrid;
+    void* dst1 = (nb >= 2) ? (((nb - 2) % 2 == 0) ? out : wsgrid) : nullptr;
+    if (!g->periodic) {
+        if (dst0 && dst0 != g->src0 && dst0 != in) g->halo_dst0 = dst0;
+        if (dst1 && dst1 != g->src0 && dst1 != in) g->halo_dst1 = dst1;
+    }
+    return nb * (int64_t)g->ntiles;
+}
+
+cudaError_t tb_launch(const ebisu_plan_s* p, const TBParams& prm, int grid, size_t smem, cudaStream_t st)
+{
+    switch (p->dtype) {
+    case EBISU_F64: return tb_launch_f64(p->ndim, p->shape, p->radius, prm, grid, smem, st);
+    case EBISU_F32: return tb_launch_f32(p->ndim, p->shape, p->radius, prm, grid, smem, st);
+    default: return tb_launch_bf16(p->ndim, p->shape, p->radius, prm, grid, smem, st);
+    }
+}
+
+cudaError_t tb_occupancy(const ebisu_plan_s* p, size_t smem, int* blocks)
+{
+    switch (p->dtype) {
+    case EBISU_F64: return tb_occupancy_f64(p->ndim, p->shape, p->radius, smem, blocks);
+    case EBISU_F32: return tb_occupancy_f32(p->ndim, p->shape, p->radius, smem, blocks);
+    default: return tb_occupancy_bf16(p->ndim, p->shape, p->radius, smem, blocks);
+    }
+}
+
+static NaiveParams naive_params(const ebisu_plan_s* p)
+{
+    NaiveParams a;
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < 3; ++i) a.n[i] = p->n[i];
+    a.lds = p->lds;
+    a.ld1 = p->ld1;
+    a.pad = p->pad;
+    a.periodic = p->boundary == EBISU_PERIODIC;
+    for (int k = 0; k < p->npts; ++k) a.coef[k] = p->coef[k];
+    return a;
+}
+
+cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, cudaStream_t st)
+{
+    const NaiveParams a = naive_params(p);
+    switch (p->dtype) {
+    case EBISU_F64: return naive_launch_f64(p->ndim, p->shape, p->radius, src, dst, a, st);
+    case EBISU_F32: return naive_launch_f32(p->ndim, p->shape, p->radius, src, dst, a, st);
+    default: return naive_launch_bf16(p->ndim, p->shape, p->radius, src, dst, a, st);
+    }
+}
+
+static PadParams pad_params(const ebisu_plan_s* p)
+{
+    PadParams a;
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < 3; ++i) a.n[i] = p->n[i];
+    a.lds = p->lds;
+    a.ld1 = p->ld1;
+    a.pad = p->pad;
+    a.pad1 = p->pad1;
+    return a;
+}
+
+cudaError_t pad_copy(const ebisu_plan_s* p, const void* src, void* d0, void* d1, cudaStream_t st)
+{
+    if (p->boundary == EBISU_PERIODIC || (!d0 && !d1)) return cudaSuccess;
+    const PadParams a = pad_params(p);
+    switch (p->dtype) {
+    case EBISU_F64: return pad_copy_f64(src, d0, d1, a, st);
+    case EBISU_F32: return pad_copy_f32(src, d0, d1, a, st);
+    default: return pad_copy_bf16(src, d0, d1, a, st);
+    }
+}
+
+}  // namespace ebisu
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+const char* ebisu_status_string(int s)
+{
+    switch (s) {
+    case EBISU_OK: return "ok";
+    case EBISU_ERR_INVALID_ARG: return "invalid argument";
+    case EBISU_ERR_UNSUPPORTED: return "unsupported stencil, size or parameters";
+    case EBISU_ERR_CUDA: return "CUDA error";
+    case EBISU_ERR_OOM: return "out of host memory";
+    case EBISU_ERR_BUDGET: return "request exceeds the HBM budget";
+    case EBISU_ERR_TIMEOUT: return "a device-side wait timed out";
+    case EBISU_ERR_DEVICE_FAULT: return "kernel reported an inconsistent state";
+    case EBISU_ERR_NOT_READY: return "not ready";
+    default: return "unknown status";
+    }
+}
+
+int ebisu_version(void) { return 10000; }
+
+const char* ebisu_last_cuda_error(void) { return g_err; }
+
+int ebisu_plan_create(int ndim, const int64_t* dims, int shape, int radius, const double* coeffs, int dtype,
+                      int boundary, ebisu_plan_t* out)
+{
+    if (!out || !dims || !coeffs) return EBISU_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (ndim != 2 && ndim != 3) return EBISU_ERR_INVALID_ARG;
+    if (shape != EBISU_STAR && shape != EBISU_BOX) return EBISU_ERR_INVALID_ARG;
+    if (dtype != EBISU_F64 && dtype != EBISU_F32 && dtype != EBISU_BF16) return EBISU_ERR_INVALID_ARG;
+    if (boundary != EBISU_DIRICHLET && boundary != EBISU_PERIODIC) return EBISU_ERR_INVALID_ARG;
+    if (radius < 1) return EBISU_ERR_INVALID_ARG;
+    if ((shape == EBISU_STAR && radius > 3) || (shape == EBISU_BOX && radius > 2)) return EBISU_ERR_UNSUPPORTED;
+    for (int i = 0; i < ndim; ++i) {
+        if (dims[i] < 1) return EBISU_ERR_INVALID_ARG;
+        if (boundary == EBISU_PERIODIC && dims[i] < 2 * radius + 1) return EBISU_ERR_UNSUPPORTED;
+        if (dims[i] > (int64_t)1 << 31) return EBISU_ERR_UNSUPPORTED;
+    }
+    ebisu_plan_s* p = new (std::nothrow) ebisu_plan_s();
+    if (!p) return EBISU_ERR_OOM;
+    p->ndim = ndim;
+    p->shape = shape;
+    p->radius = radius;
+    p->dtype = dtype;
+    p->boundary = boundary;
+    for (int i = 0; i < ndim; ++i) p->dims[i] = dims[i];
+    p->npts = (shape == EBISU_STAR) ? 2 * ndim * radius + 1
+                                    : (ndim == 3 ? (2 * radius + 1) * (2 * radius + 1) * (2 * radius + 1)
+                                                 : (2 * radius + 1) * (2 * radius + 1));
+    for (int k = 0; k < p->npts; ++k) p->coef[k] = coeffs[k];
+    p->esize = (dtype == EBISU_F64) ? 8 : (dtype == EBISU_F32 ? 4 : 2);
+    p->pad = (boundary == EBISU_DIRICHLET) ? radius : 0;
+    if (ndim == 2) {
+        p->n[0] = dims[0];
+        p->n[1] = 1;
+        p->n[2] = dims[1];
+        p->pad1 = 0;
+        p->ext[0] = dims[0] + 2 * p->pad;
+        p->ext[1] = 1;
+        p->ext[2] = dims[1] + 2 * p->pad;
+        p->lds = p->ext[2];
+        p->ld1 = 0;
+    } else {
+        for (int i = 0; i < 3; ++i) p->n[i] = dims[i];
+        p->pad1 = p->pad;
+        for (int i = 0; i < 3; ++i) p->ext[i] = dims[i] + 2 * p->pad;
+        p->lds = p->ext[1] * p->ext[2];
+        p->ld1 = p->ext[2];
+    }
+    p->elems = p->ext[0] * p->ext[1] * p->ext[2];
+    ebisu_params best;
+    double pred = 0;
+    if (rank_candidates(p, 1000, &best, &pred, 1) < 1) {
+        // fall back to the smallest legal blocked configuration
+        memset(&best, 0, sizeof(best));
+        best.tile_x = 64;
+        best.tile_y = 8;
+        best.depth = 1;
+        best.ctas_per_sm = 1;
+        best.threads = kThreads;
+    }
+    p->prm = best;
+    *out = p;
+    return EBISU_OK;
+}
+
+int ebisu_plan_destroy(ebisu_plan_t plan)
+{
+    delete plan;
+    return EBISU_OK;
+}
+
+int ebisu_plan_npoints(ebisu_plan_t plan, int* npts)
+{
+    if (!plan || !npts) return EBISU_ERR_INVALID_ARG;
+    *npts = plan->npts;
+    return EBISU_OK;
+}
+
+int ebisu_plan_grid_elems(ebisu_plan_t plan, int64_t* elems)
+{
+    if (!plan || !elems) return EBISU_ERR_INVALID_ARG;
+    *elems = plan->elems;
+    return EBISU_OK;
+}
+
+int ebisu_plan_get_params(ebisu_plan_t plan, ebisu_params* q)
+{
+    if (!plan || !q) return EBISU_ERR_INVALID_ARG;
+    *q = plan->prm;
+    return EBISU_OK;
+}
+
+int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* q)
+{
+    if (!plan || !q) return EBISU_ERR_INVALID_ARG;
+    ebisu_params v = *q;
+    v.threads = kThreads;
+    if (v.ctas_per_sm == 0) v.ctas_per_sm = 1;
+    const int rc = check_params(plan, v);
+    if (rc != EBISU_OK) return rc;
+    plan->prm = v;
+    return EBISU_OK;
+}
+
+int ebisu_plan_workspace_bytes(ebisu_plan_t plan, size_t* bytes)
+{
+    if (!plan || !bytes) return EBISU_ERR_INVALID_ARG;
+    *bytes = kControlBytes + align_up((size_t)plan->elems * plan->esize, kAlign);
+    return EBISU_OK;
+}
+
+static int run_common(ebisu_plan_t p, const void* in, void* out, int64_t steps, void* ws, void* stream,
+                      bool naive, int debug_stall)
+{
+    if (!p || !in || !out || !ws) return EBISU_ERR_INVALID_ARG;
+    if (steps < 0) return EBISU_ERR_INVALID_ARG;
+    if (((uintptr_t)ws) % kAlign != 0) return EBISU_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)p->elems * p->esize;
+    void* wsgrid = (char*)ws + kControlBytes;
+    cudaError_t e = cudaMemsetAsync(ws, 0, kControlBytes, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (steps == 0) {
+        if (in != out) {
+            e = cudaMemcpyAsync(out, in, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return fail_cuda(e);
+        }
+        return EBISU_OK;
+    }
+    if (naive || p->prm.variant == 1) {
+        // one launch per step; buffers alternate so that the last lands in out
+        const void* src = in;
+        if (in == out && (steps % 2 == 1)) {
+            e = cudaMemcpyAsync(wsgrid, in, bytes, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return fail_cuda(e);
+            src = wsgrid;
+        }
+        void* d0 = ((steps - 1) % 2 == 0) ? out : wsgrid;
+        void* d1 = (steps >= 2) ? (((steps - 2) % 2 == 0) ? out : wsgrid) : nullptr;
+        void* h0 = (d0 != src && d0 != in) ? d0 : nullptr;
+        void* h1 = (d1 && d1 != src && d1 != in) ? d1 : nullptr;
+        e = pad_copy(p, src, h0, h1, st);
+        if (e != cudaSuccess) return fail_cuda(e);
+        for (int64_t s = 0; s < steps; ++s) {
+            void* dst = ((steps - 1 - s) % 2 == 0) ? out : wsgrid;
+            e = naive_launch(p, src, dst, st);
+            if (e != cudaSuccess) return fail_cuda(e);
+            src = dst;
+        }
+        return EBISU_OK;
+    }
+    const ebisu_params& q = p->prm;
+    const int d = (int)std::min<int64_t>(q.depth, steps);
+    const int64_t nb = (steps + d - 1) / d;
+    const bool copy_in = (in == out) && (nb % 2 == 1);
+    if (copy_in) {
+        e = cudaMemcpyAsync(wsgrid, in, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return fail_cuda(e);
+    }
+    TBParams prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.nitems = fill_grid_desc(p, in, out, wsgrid, steps, copy_in, &prm.g);
+    prm.grids = nullptr;
+    prm.items = nullptr;
+    prm.ctl = (Control*)ws;
+    prm.timeout_ns = wait_timeout_ns();
+    prm.debug_stall = debug_stall;
+    ebisu_params qd = q;
+    qd.depth = d;
+    prm.smem_plane = (int32_t)plane_capacity(p, qd);
+    const size_t smem = tb_smem_bytes(p, qd);
+    int occ = 0;
+    e = tb_occupancy(p, smem, &occ);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (occ < 1) return EBISU_ERR_UNSUPPORTED;
+    const DeviceInfo& dv = device_info();
+    int64_t grid = (int64_t)std::min(occ, q.ctas_per_sm) * dv.sms;
+    grid = std::min<int64_t>(grid, prm.nitems);
+    e = tb_launch(p, prm, (int)grid, smem, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return EBISU_OK;
+}
+
+int ebisu_run(ebisu_plan_t plan, const void* in, void* out, int64_t steps, void* workspace, void* stream)
+{
+    return run_common(plan, in, out, steps, workspace, stream, false, 0);
+}
+
+int ebisu_run_naive(ebisu_plan_t plan, const void* in, void* out, int64_t steps, void* workspace, void* stream)
+{
+    return run_common(plan, in, out, steps, workspace, stream, true, 0);
+}
+
+// Test hook (not in the public header): a blocked run whose first dependency
+// wait targets a count nothing reaches, so the bounded wait must give up and
+// report EBISU_ERR_TIMEOUT.
+int ebisu_debug_run_stalled(ebisu_plan_t plan, const void* in, void* out, int64_t steps, void* workspace,
+                            void* stream)
+{
+    return run_common(plan, in, out, steps, workspace, stream, false, 1);
+}
+
+int ebisu_sync(void* workspace, void* stream)
+{
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (!workspace) return EBISU_OK;
+    int st = 0;
+    e = cudaMemcpy(&st, workspace, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (st != 0) {
+        cudaMemset(workspace, 0, sizeof(int));
+        return st;
+    }
+    return EBISU_OK;
+}
+
+int ebisu_reduce(ebisu_plan_t p, const void* a, const void* b, double* result, void* ws, void* stream)
+{
+    if (!p || !a || !result || !ws) return EBISU_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    PadParams g = pad_params(p);
+    double* part = (double*)((char*)ws + kControlBytes);
+    double* fin = (double*)((char*)ws + 2048);
+    int64_t nparts = 0;
+    cudaError_t e;
+    switch (p->dtype) {
+    case EBISU_F64: e = reduce_partial_f64(a, b, part, g, &nparts, st); break;
+    case EBISU_F32: e = reduce_partial_f32(a, b, part, g, &nparts, st); break;
+    default: e = reduce_partial_bf16(a, b, part, g, &nparts, st); break;
+    }
+    if (e != cudaSuccess) return fail_cuda(e);
+    e = reduce_final(part, nparts, fin, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    e = cudaMemcpyAsync(result, fin, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return EBISU_OK;
+}
+
+int ebisu_probe_device(double* out)
+{
+    if (!out) return EBISU_ERR_INVALID_ARG;
+    cudaError_t e = probe_device(out);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return EBISU_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// plan.h -- host-side plan object and helpers shared by the C-ABI files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/ebisu.h"
+#include "common.h"
+#include "dispatch.h"
+
+struct ebisu_plan_s {
+    int ndim = 0, shape = 0, radius = 0, dtype = 0, boundary = 0;
+    int64_t dims[3] = {0, 0, 0};  // interior extents, slowest first (as given)
+    int npts = 0;
+    double coef[ebisu::kMaxPoints] = {};
+    ebisu_params prm{};
+    // streaming coordinates (s, p1, p2); p1 is a dummy axis in 2D
+    int64_t n[3] = {1, 1, 1};
+    int64_t ext[3] = {1, 1, 1};  // stored extents
+    int64_t lds = 0, ld1 = 0;
+    int pad = 0, pad1 = 0;
+    size_t esize = 8;
+    int64_t elems = 0;
+};
+
+namespace ebisu {
+
+constexpr int kThreads = 256;      // threads per CTA of the blocked kernel
+constexpr int kStagePerThread = 16; // register-staged plane elements per thread
+constexpr int kPrefetch = 4;        // input planes in flight (cp.async)
+
+struct DeviceInfo {
+    int device = -1;
+    int sms = 0;
+    size_t smem_optin = 0;
+    size_t smem_per_sm = 0;
+    char name[256] = {0};
+    // measured rates (filled lazily by the tuner)
+    double f64 = 0, f32 = 0, lds = 0, barrier_s = 0;
+};
+
+// Cached properties of the current device (queried once per device).
+const DeviceInfo& device_info();
+// Measured throughputs for the cost model; runs the microbenchmarks once per
+// process (or uses defaults from a host without a GPU).
+const DeviceInfo& device_rates();
+
+void set_cuda_error(cudaError_t e);
+int fail_cuda(cudaError_t e);
+
+int ring_q(int radius);   // slots of a level-1.. ring (2r+2)
+int ring_q0(int radius);  // slots of the input ring (2r+1+prefetch)
+// Elements per ring plane and dynamic shared memory of a parameter set.
+int64_t plane_capacity(const ebisu_plan_s* p, const ebisu_params& q);
+size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q);
+// Validate a parameter set against the plan and the device.
+int check_params(const ebisu_plan_s* p, const ebisu_params& q);
+// Cost-model ranking (tune.cpp): writes up to `cap` candidates, best first.
+int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, double* pred, int cap);
+// Cost model of one parameter set (tune.cpp).
+double model_pp(const ebisu_plan_s* p, const ebisu_params& q, int64_t steps, int* bound, double* valid);
+
+// Fill a GridDesc for one run of `steps` steps; returns the number of items.
+int64_t fill_grid_desc(const ebisu_plan_s* p, const void* in, void* out, void* wsgrid, int64_t steps,
+                       bool in_copied_to_ws, GridDesc* g);
+
+cudaError_t tb_launch(const ebisu_plan_s* p, const TBParams& prm, int grid, size_t smem, cudaStream_t st);
+cudaError_t tb_occupancy(const ebisu_plan_s* p, size_t smem, int* blocks);
+cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, cudaStream_t st);
+cudaError_t pad_copy(const ebisu_plan_s* p, const void* src, void* d0, void* d1, cudaStream_t st);
+
+int64_t wait_timeout_ns();
+
+}  // namespace ebisu

@@ -1,0 +1,144 @@
+// stencil.cuh -- device-side stencil definition shared by every CUDA kernel.
+//
+// The update is the Jacobi sweep of Section 2.1 (Listings 1-3, shapes of
+// Table 2): new(x) = sum_k c_k * old(x + o_k).  Offsets are generated at
+// compile time in canonical order -- lexicographic in (dz, dy, dx) -- and the
+// sum is always taken as
+//     acc = c_0 * u_0;  acc = fma(c_k, u_k, acc),  k = 1 .. P-1,
+// with explicit round-to-nearest intrinsics, so every kernel of the library
+// (naive, temporally blocked, batched) produces bit-identical cells.
+#pragma once
+#include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+namespace ebisu {
+
+enum { kStar = 0, kBox = 1 };
+
+// ---------------------------------------------------------------------------
+// Canonical offsets, expressed in streaming coordinates: `s` is the slowest
+// axis (y in 2D, z in 3D) along which tiles are streamed; `p1`, `p2` are the
+// in-plane axes (p1 is a dummy axis of extent 1 in 2D, p2 is x).
+
+template <int DIM, int SHAPE, int R>
+struct Stencil {
+    static constexpr int kR = R;
+    static constexpr int kDim = DIM;
+    static constexpr int kRP1 = (DIM == 3) ? R : 0;  // radius along p1
+    static constexpr int P = (SHAPE == kStar) ? (2 * DIM * R + 1)
+                                              : ((DIM == 3) ? (2 * R + 1) * (2 * R + 1) * (2 * R + 1)
+                                                            : (2 * R + 1) * (2 * R + 1));
+    struct Table {
+        int ds[P];
+        int d1[P];
+        int d2[P];
+    };
+    static constexpr Table make()
+    {
+        Table t{};
+        int n = 0;
+        const int zr = (DIM == 3) ? R : 0;
+        for (int a = -zr; a <= zr; ++a)
+            for (int b = -R; b <= R; ++b)
+                for (int c = -R; c <= R; ++c) {
+                    const int nz = (a != 0) + (b != 0) + (c != 0);
+                    if (SHAPE == kStar && nz > 1) continue;
+                    if (DIM == 3) {
+                        t.ds[n] = a; t.d1[n] = b; t.d2[n] = c;
+                    } else {
+                        t.ds[n] = b; t.d1[n] = 0; t.d2[n] = c;
+                    }
+                    ++n;
+                }
+        return t;
+    }
+    static constexpr Table kOff = make();
+};
+
+// ---------------------------------------------------------------------------
+// Storage / compute type traits.  C is the accumulation type.
+
+template <class T>
+struct DT;
+
+template <>
+struct DT<double> {
+    using C = double;
+    __device__ static __forceinline__ C load(const double* p) { return __ldcg(p); }
+    __device__ static __forceinline__ double raw(const double* p) { return __ldcg(p); }
+    __device__ static __forceinline__ C load_ro(const double* p) { return __ldg(p); }
+    __device__ static __forceinline__ C widen(double v) { return v; }
+    __device__ static __forceinline__ double narrow(C v) { return v; }
+    __device__ static __forceinline__ C mul(C a, C b) { return __dmul_rn(a, b); }
+    __device__ static __forceinline__ C fma(C a, C b, C c) { return __fma_rn(a, b, c); }
+    __host__ __device__ static __forceinline__ C coef(double v) { return v; }
+};
+
+template <>
+struct DT<float> {
+    using C = float;
+    __device__ static __forceinline__ C load(const float* p) { return __ldcg(p); }
+    __device__ static __forceinline__ float raw(const float* p) { return __ldcg(p); }
+    __device__ static __forceinline__ C load_ro(const float* p) { return __ldg(p); }
+    __device__ static __forceinline__ C widen(float v) { return v; }
+    __device__ static __forceinline__ float narrow(C v) { return v; }
+    __device__ static __forceinline__ C mul(C a, C b) { return __fmul_rn(a, b); }
+    __device__ static __forceinline__ C fma(C a, C b, C c) { return __fmaf_rn(a, b, c); }
+    __host__ __device__ static __forceinline__ C coef(double v) { return (float)v; }
+};
+
+template <>
+struct DT<__nv_bfloat16> {
+    using C = float;
+    __device__ static __forceinline__ C load(const __nv_bfloat16* p)
+    {
+        unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p));
+        return __uint_as_float(((unsigned)b) << 16);
+    }
+    __device__ static __forceinline__ __nv_bfloat16 raw(const __nv_bfloat16* p)
+    {
+        unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p));
+        return __ushort_as_bfloat16(b);
+    }
+    __device__ static __forceinline__ C load_ro(const __nv_bfloat16* p)
+    {
+        unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(p));
+        return __uint_as_float(((unsigned)b) << 16);
+    }
+    __device__ static __forceinline__ C widen(__nv_bfloat16 v) { return __bfloat162float(v); }
+    __device__ static __forceinline__ __nv_bfloat16 narrow(C v) { return __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ C mul(C a, C b) { return __fmul_rn(a, b); }
+    __device__ static __forceinline__ C fma(C a, C b, C c) { return __fmaf_rn(a, b, c); }
+    __host__ __device__ static __forceinline__ C coef(double v) { return (float)v; }
+};
+
+// Periodic index wrap (any i; the common in-range case costs two compares).
+__device__ __forceinline__ int64_t wrap_idx(int64_t i, int64_t n)
+{
+    if (i >= 0 && i < n) return i;
+    const int64_t m = i % n;
+    return m < 0 ? m + n : m;
+}
+
+// Wall-clock time in ns (bounded waits).
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(unsigned* p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+}  // namespace ebisu

@@ -1,0 +1,434 @@
+// tb_kernel.cuh -- persistent temporally blocked stencil kernel (2D and 3D).
+//
+// What the paper's method does, and how this kernel maps it to sm_103a:
+//  * Tile by tile (Section 4.1): a CTA owns one large output tile at a time
+//    and runs all `depth` fused time steps of it before taking the next one;
+//    tiles come from a device-wide work queue (an atomic counter), so one
+//    persistent launch covers every tile of every temporal block.
+//  * N.5-D streaming (Section 2.1.3): the tile is streamed along the slowest
+//    axis (y in 2D, z in 3D); each streamed plane (a row in 2D) passes
+//    through all time levels while it is on chip.
+//  * Circular multi-queue (Section 4.2): every time level keeps a ring of
+//    planes in shared memory; a plane's slot is its index modulo the ring
+//    length (a compile-time constant, so the modulo is a multiply-shift).
+//  * Lazy streaming (Section 4.3.2): level s lags level s-1 by r+1 planes, so
+//    everything a level reads was written before the previous barrier and a
+//    streamed plane costs exactly one __syncthreads.
+//  * Prefetching (Section 4.3.1): input planes are copied global -> shared
+//    with cp.async PF planes ahead of use (Little's law: enough bytes in
+//    flight to cover the memory latency at the bandwidth the tile needs).
+//  * Overlapped tiling (Section 2.1.2, SM tiling): each level computes only
+//    the trapezoid it needs, shrinking by r per level, so the redundant work
+//    is the paper's 1 - V_SMtile and nothing more.
+//  * Dependencies between temporal blocks replace the grid barrier: an item
+//    of block b waits (bounded spin on %globaltimer) until every tile of block
+//    b-1 of the same problem is done.  Items are popped in order, so a wait
+//    only ever targets items held by running CTAs: no deadlock and no
+//    co-residency requirement.
+//  * Dirichlet pads are re-imposed at every level: a pad cell of level s is
+//    copied from the same position of level s-1's ring (and level 0 loaded it
+//    from global memory), so no intermediate level ever computes a pad cell.
+//    Periodic neighbours wrap when level 0 is loaded.
+#pragma once
+#include "common.h"
+#include "stencil.cuh"
+
+namespace ebisu {
+
+template <int R, int PF>
+struct RingGeom {
+    static constexpr int Q0 = 2 * R + 1 + PF;  // input ring (level 0)
+    static constexpr int Q = 2 * R + 2;        // rings of levels 1 .. d-1
+};
+
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// quotient of i / d for 0 <= i < 2^22 using a float reciprocal
+__device__ __forceinline__ int fast_div(int i, float inv_d, int d)
+{
+    int q = (int)(((float)i + 0.5f) * inv_d);
+    q -= (q * d > i);
+    q += ((q + 1) * d <= i);
+    return q;
+}
+
+enum { kLoadElem = 0, kLoadPairs = 1, kLoadStaged = 2 };
+
+template <class T, int DIM, int SHAPE, int R, int NT, int ILP, int PF, int STG>
+__global__ void __launch_bounds__(NT, 2) tb_kernel(const __grid_constant__ TBParams prm)
+{
+    using St = Stencil<DIM, SHAPE, R>;
+    using D = DT<T>;
+    using C = typename D::C;
+    constexpr int P = St::P;
+    constexpr int Q0 = RingGeom<R, PF>::Q0;
+    constexpr int Q = RingGeom<R, PF>::Q;
+    constexpr int RP1 = St::kRP1;
+    constexpr bool kCoefRegs = (P <= 32);
+    constexpr auto OFF = St::kOff;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* const ring = reinterpret_cast<T*>(smem_raw);
+    __shared__ GridDesc sg;
+    __shared__ C s_coef[kCoefRegs ? 1 : P];
+    __shared__ int s_cmd[4];
+
+    const int tid = threadIdx.x;
+    Control* const ctl = prm.ctl;
+    const int plane_cap = prm.smem_plane;
+
+    for (;;) {
+        // ---- pop the next work item ---------------------------------------
+        if (tid == 0) {
+            int64_t it = -1;
+            if (*(volatile int*)&ctl->status == 0) it = (int64_t)atomicAdd(&ctl->next_item, 1u);
+            int g = 0, b = 0, tl = 0;
+            if (it >= 0 && it < prm.nitems) {
+                if (prm.items) {
+                    g = prm.items[3 * it + 0];
+                    b = prm.items[3 * it + 1];
+                    tl = prm.items[3 * it + 2];
+                } else {
+                    b = (int)(it / prm.g.ntiles);
+                    tl = (int)(it % prm.g.ntiles);
+                }
+            } else {
+                it = -1;
+            }
+            s_cmd[0] = (it < 0) ? -1 : g;
+            s_cmd[1] = b;
+            s_cmd[2] = tl;
+            s_cmd[3] = (int)it;
+        }
+        __syncthreads();
+        const int gi = s_cmd[0];
+        const int blk = s_cmd[1];
+        const int tile = s_cmd[2];
+        const int item = s_cmd[3];
+        if (gi < 0) return;
+        {   // copy the problem descriptor into shared memory
+            const GridDesc* srcd = prm.grids ? (prm.grids + gi) : &prm.g;
+            const int* w = reinterpret_cast<const int*>(srcd);
+            int* dsm = reinterpret_cast<int*>(&sg);
+            for (int i = tid; i < (int)(sizeof(GridDesc) / sizeof(int)); i += NT) dsm[i] = w[i];
+        }
+        __syncthreads();
+
+        // ---- wait until the previous temporal block is complete -------------
+        if (tid == 0) {
+            int ok = 1;
+            if (blk > 0 || prm.debug_stall) {
+                const unsigned target = (unsigned)blk * (unsigned)sg.ntiles + (prm.debug_stall ? 1u : 0u);
+                const unsigned* cnt = &ctl->done[sg.grid_id];
+                if (ld_acquire_u32(cnt) < target) {
+                    const uint64_t t0 = global_ns();
+                    unsigned ns = 32;
+                    while (ld_acquire_u32(cnt) < target) {
+                        if (*(volatile int*)&ctl->status != 0) { ok = 0; break; }
+                        if (global_ns() - t0 > (uint64_t)prm.timeout_ns) {
+                            atomicCAS(&ctl->status, 0, 6 /* EBISU_ERR_TIMEOUT */);
+                            atomicExch(&ctl->wait_where, (unsigned)item);
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(ns);
+                        ns = ns < 1024 ? ns * 2 : ns;
+                    }
+                }
+            }
+            s_cmd[0] = ok;
+        }
+        __syncthreads();
+        if (!s_cmd[0]) return;
+
+        // ---- geometry of this item ------------------------------------------
+        const bool last = (blk == sg.nblocks - 1);
+        const int d = last ? sg.last_depth : sg.depth;
+        const bool dst_is_out = ((sg.nblocks - 1 - blk) % 2) == 0;
+        T* const dst = reinterpret_cast<T*>(dst_is_out ? sg.out : sg.ws);
+        const T* const src = (blk == 0) ? reinterpret_cast<const T*>(sg.src0)
+                                        : reinterpret_cast<const T*>(dst_is_out ? sg.ws : sg.out);
+        const bool per = sg.periodic != 0;
+        const int64_t n0 = sg.n[0];
+        const int n1 = (int)sg.n[1], n2 = (int)sg.n[2];
+        const int pad = sg.pad;
+        const int pad1 = (DIM == 3) ? pad : 0;
+        const int64_t lds = sg.lds;
+        const int ld1 = (int)sg.ld1;
+        // 4- and 8-byte types always use element copies (compile-time)
+        const int mode = (sizeof(T) == 2) ? sg.load_mode : (int)kLoadElem;
+        const int t2i = tile % sg.nt[2];
+        const int t1i = (tile / sg.nt[2]) % sg.nt[1];
+        const int tsi = tile / (sg.nt[2] * sg.nt[1]);
+        const int64_t as = (int64_t)tsi * sg.tile[0], bs = min(as + sg.tile[0], n0);
+        const int a1 = t1i * sg.tile[1], b1 = min(a1 + sg.tile[1], n1);
+        const int a2 = t2i * sg.tile[2], b2 = min(a2 + sg.tile[2], n2);
+
+        // coefficients
+        C cr[kCoefRegs ? P : 1];
+        if constexpr (kCoefRegs) {
+#pragma unroll
+            for (int k = 0; k < P; ++k) cr[k] = D::coef(sg.coef[k]);
+        } else {
+            for (int k = tid; k < P; k += NT) s_coef[k] = D::coef(sg.coef[k]);
+            __syncthreads();
+        }
+
+        // region of time level s along each axis: [a - r(d-s), b + r(d-s)),
+        // clipped to the padded array for Dirichlet grids.
+        auto lo_s = [&](int64_t a, int rr, int s, int padax) -> int64_t {
+            const int64_t v = a - (int64_t)rr * (d - s);
+            return per ? v : max(v, (int64_t)-padax);
+        };
+        auto hi_s = [&](int64_t b, int64_t n, int rr, int s, int padax) -> int64_t {
+            const int64_t v = b + (int64_t)rr * (d - s);
+            return per ? v : min(v, n + padax);
+        };
+        const int64_t slo0 = lo_s(as, R, 0, pad), shi0 = hi_s(bs, n0, R, 0, pad);
+        const int lo01 = (int)lo_s(a1, RP1, 0, pad1), hi01 = (int)hi_s(b1, n1, RP1, 0, pad1);
+        const int lo02 = (int)lo_s(a2, R, 0, pad), hi02 = (int)hi_s(b2, n2, R, 0, pad);
+        const int E1 = hi01 - lo01, E2 = hi02 - lo02;
+        const int E2p = (E2 + 3) & ~1;  // ring row pitch: even, room for the pair-load shift
+        const int plane0 = E1 * E2;
+        if (E1 * E2p > plane_cap || (mode == kLoadStaged && plane0 > STG * NT)) {
+            if (tid == 0) atomicCAS(&ctl->status, 0, 7 /* EBISU_ERR_DEVICE_FAULT */);
+            return;
+        }
+        const float invE2 = 1.0f / (float)E2;
+        const int safe_off = (E1 / 2) * E2p + E2 / 2;  // >= R away from every plane edge
+
+        // stored element offset of (ps, q1, q2), interior coordinates
+        auto gplane = [&](int64_t ps) -> int64_t {
+            if (per) return wrap_idx(ps, n0) * lds;
+            return (ps + pad) * lds;
+        };
+        auto ginplane = [&](int q1, int q2) -> int64_t {
+            if (per) {
+                const int64_t y = (DIM == 3) ? wrap_idx(q1, n1) : 0;
+                return y * ld1 + wrap_idx(q2, n2);
+            }
+            return (int64_t)(q1 + pad1) * ld1 + (q2 + pad);
+        };
+        // ring slot of plane ps at level lev (0 = input ring)
+        auto ring_plane = [&](int lev, int64_t ps) -> T* {
+            const unsigned rel = (unsigned)(ps - slo0);
+            if (lev == 0) return ring + (size_t)(rel % Q0) * plane_cap;
+            return ring + ((size_t)Q0 + (size_t)(lev - 1) * Q + (rel % Q)) * plane_cap;
+        };
+        // shift of a level-0 plane in pair-load mode: parity of its first
+        // stored element (every row of a plane shares it, see host checks)
+        auto pshift = [&](int64_t ps) -> int {
+            if (mode != kLoadPairs) return 0;
+            return (int)((gplane(ps) + ginplane(lo01, lo02)) & 1);
+        };
+
+        // ---- first temporal block: fill the Dirichlet pads of the buffers ---
+        if (blk == 0 && !per && (sg.halo_dst0 || sg.halo_dst1)) {
+            T* h0 = reinterpret_cast<T*>(sg.halo_dst0);
+            T* h1 = reinterpret_cast<T*>(sg.halo_dst1);
+            const T* s0 = reinterpret_cast<const T*>(sg.src0);
+            const bool t12 = (DIM == 3 && (a1 == 0 || b1 == n1)) || a2 == 0 || b2 == n2;
+            const bool touches = (as == 0) || (bs == n0) || t12;
+            if (touches) {
+                const int64_t xs0 = (as == 0) ? -pad : as, xs1 = (bs == n0) ? n0 + pad : bs;
+                const int x10 = (a1 == 0) ? -pad1 : a1, x11 = (b1 == n1) ? n1 + pad1 : b1;
+                const int x20 = (a2 == 0) ? -pad : a2, x21 = (b2 == n2) ? n2 + pad : b2;
+                const int w1 = x11 - x10, w2 = x21 - x20;
+                for (int64_t ps = xs0; ps < xs1; ++ps) {
+                    const bool hp = (ps < 0 || ps >= n0);
+                    if (!hp && !t12) continue;
+                    const int64_t pb = gplane(ps);
+                    for (int i = tid; i < w1 * w2; i += NT) {
+                        const int q1 = x10 + i / w2, q2 = x20 + i % w2;
+                        if (!(hp || q1 < 0 || q1 >= n1 || q2 < 0 || q2 >= n2)) continue;
+                        const int64_t g = pb + ginplane(q1, q2);
+                        const T v = D::raw(s0 + g);
+                        if (h0) h0[g] = v;
+                        if (h1) h1[g] = v;
+                    }
+                }
+            }
+        }
+
+        // ---- level-0 plane loads --------------------------------------------
+        // Element mode: one cp.async per element (any alignment, wraps).
+        // Pair mode (2-byte types): 4-byte cp.async of aligned element pairs;
+        //   the plane is stored shifted by the parity of its first element.
+        // Staged mode: registers, loaded one iteration ahead (fallback).
+        constexpr int kStg = (sizeof(T) == 2) ? STG : 1;
+        T stage[kStg];
+        auto issue_plane = [&](int64_t ps) {
+            T* rp = ring_plane(0, ps);
+            const int64_t pb = gplane(ps);
+            if (mode == kLoadElem) {
+                for (int i = tid; i < plane0; i += NT) {
+                    const int r1 = (DIM == 3) ? fast_div(i, invE2, E2) : 0;
+                    const int c2 = i - r1 * E2;
+                    cp_async(rp + r1 * E2p + c2, src + pb + ginplane(lo01 + r1, lo02 + c2), (int)sizeof(T));
+                }
+            } else if (mode == kLoadPairs) {
+                const int sh = pshift(ps);
+                const int npair = (E2 + sh + 1) >> 1;
+                const int64_t last_elem = sg.total_elems - 1;
+                for (int i = tid; i < E1 * npair; i += NT) {
+                    const int r1 = (DIM == 3) ? i / npair : 0;
+                    const int k = i - r1 * npair;
+                    const int64_t g0 = pb + ginplane(lo01 + r1, lo02) - sh + 2 * k;
+                    T* sp = rp + r1 * E2p + 2 * k;
+                    if (g0 + 1 <= last_elem) {
+                        cp_async(sp, src + g0, 4);
+                    } else {
+                        sp[0] = D::raw(src + g0);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kStg; ++k) {
+                    const int i = tid + k * NT;
+                    if (i < plane0) {
+                        const int r1 = (DIM == 3) ? fast_div(i, invE2, E2) : 0;
+                        const int c2 = i - r1 * E2;
+                        stage[k] = D::raw(src + pb + ginplane(lo01 + r1, lo02 + c2));
+                    }
+                }
+            }
+        };
+        auto finish_staged = [&](int64_t ps) {
+            T* rp = ring_plane(0, ps);
+#pragma unroll
+            for (int k = 0; k < kStg; ++k) {
+                const int i = tid + k * NT;
+                if (i < plane0) {
+                    const int r1 = (DIM == 3) ? fast_div(i, invE2, E2) : 0;
+                    rp[r1 * E2p + (i - r1 * E2)] = stage[k];
+                }
+            }
+        };
+
+        // ---- one plane of time level s (1 <= s <= d) ---------------------------
+        auto compute_plane = [&](int s, int64_t ps) {
+            const int l1 = (int)lo_s(a1, RP1, s, pad1), h1 = (int)hi_s(b1, n1, RP1, s, pad1);
+            const int l2 = (int)lo_s(a2, R, s, pad), h2 = (int)hi_s(b2, n2, R, s, pad);
+            const int R2 = h2 - l2;
+            const int cnt = (h1 - l1) * R2;
+            const float invR2 = 1.0f / (float)R2;
+            const bool to_global = (s == d);
+            T* const outp = to_global ? nullptr : ring_plane(s, ps);
+            T* const gout = to_global ? dst + gplane(ps) : nullptr;
+            const int sh_c = (s == 1) ? pshift(ps) : 0;
+            const T* const self = ring_plane(s - 1, ps) + sh_c;
+            const bool pad_plane = !per && (ps < 0 || ps >= n0);
+            // any pad cell in this plane's region?
+            const bool edge = !per && (pad_plane || l1 < 0 || h1 > n1 || l2 < 0 || h2 > n2);
+            if (pad_plane) {  // keep the input values: copy from the level below
+                for (int i = tid; i < cnt; i += NT) {
+                    const int r1 = (DIM == 3) ? fast_div(i, invR2, R2) : 0;
+                    const int off = (l1 + r1 - lo01) * E2p + (l2 + (i - r1 * R2) - lo02);
+                    outp[off] = self[off];
+                }
+                return;
+            }
+            const T* base[2 * R + 1];
+#pragma unroll
+            for (int k = 0; k < 2 * R + 1; ++k) {
+                const int64_t pk = ps + k - R;
+                base[k] = ring_plane(s - 1, pk) + ((s == 1) ? pshift(pk) : 0);
+            }
+            for (int i0 = tid; i0 < cnt; i0 += ILP * NT) {
+                int off[ILP], rd[ILP], q1v[ILP], q2v[ILP];
+                bool val[ILP], hal[ILP];
+#pragma unroll
+                for (int u = 0; u < ILP; ++u) {
+                    const int i = i0 + u * NT;
+                    val[u] = i < cnt;
+                    const int ii = val[u] ? i : 0;
+                    const int r1 = (DIM == 3) ? fast_div(ii, invR2, R2) : 0;
+                    const int q1 = l1 + r1, q2 = l2 + (ii - r1 * R2);
+                    q1v[u] = q1;
+                    q2v[u] = q2;
+                    hal[u] = edge && (q1 < 0 || q1 >= n1 || q2 < 0 || q2 >= n2);
+                    off[u] = (q1 - lo01) * E2p + (q2 - lo02);
+                    rd[u] = (val[u] && !hal[u]) ? off[u] : safe_off;
+                }
+                C acc[ILP];
+                {
+                    const C c0 = kCoefRegs ? cr[0] : s_coef[0];
+                    const T* bp = base[OFF.ds[0] + R] + OFF.d1[0] * E2p + OFF.d2[0];
+#pragma unroll
+                    for (int u = 0; u < ILP; ++u) acc[u] = D::mul(c0, D::widen(bp[rd[u]]));
+                }
+#pragma unroll
+                for (int k = 1; k < P; ++k) {
+                    const C ck = kCoefRegs ? cr[k] : s_coef[k];
+                    const T* bp = base[OFF.ds[k] + R] + OFF.d1[k] * E2p + OFF.d2[k];
+#pragma unroll
+                    for (int u = 0; u < ILP; ++u) acc[u] = D::fma(ck, D::widen(bp[rd[u]]), acc[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < ILP; ++u) {
+                    if (!val[u]) continue;
+                    T v = D::narrow(acc[u]);
+                    if (hal[u]) v = self[off[u]];
+                    if (to_global) {
+                        if (!hal[u]) gout[ginplane(q1v[u], q2v[u])] = v;
+                    } else {
+                        outp[off[u]] = v;
+                    }
+                }
+            }
+        };
+
+        // ---- stream the tile ----------------------------------------------------
+        auto lag = [&](int s) -> int64_t { return (int64_t)R + (int64_t)(s - 1) * (R + 1); };
+        const int64_t lastp = bs - 1;  // last plane of level d
+        const int64_t niter = lastp - slo0 + lag(d) + 1;
+        if (mode != kLoadStaged) {
+            // prologue: PF planes in flight, one commit group each
+#pragma unroll 1
+            for (int k = 0; k < PF; ++k) {
+                if (slo0 + k < shi0) issue_plane(slo0 + k);
+                cp_async_commit();
+            }
+        } else {
+            issue_plane(slo0);
+            finish_staged(slo0);
+        }
+        for (int64_t j = 0; j < niter; ++j) {
+            if (mode != kLoadStaged) cp_async_wait<PF - 1>();
+            __syncthreads();
+            const int64_t pnext = slo0 + j + ((mode != kLoadStaged) ? PF : 1);
+            const bool have_next = pnext < shi0;
+            if (mode != kLoadStaged) {
+                if (have_next) issue_plane(pnext);
+                cp_async_commit();
+            } else if (have_next) {
+                issue_plane(pnext);
+            }
+            for (int s = 1; s <= d; ++s) {
+                const int64_t ps = slo0 + j - lag(s);
+                if (ps >= lo_s(as, R, s, pad) && ps < hi_s(bs, n0, R, s, pad)) compute_plane(s, ps);
+            }
+            if (mode == kLoadStaged && have_next) finish_staged(pnext);
+        }
+        if (mode != kLoadStaged) cp_async_wait<0>();
+
+        // ---- publish completion ---------------------------------------------
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            red_release_add_u32(&ctl->done[sg.grid_id], 1u);
+        }
+    }
+}
+
+}  // namespace ebisu

@@ -3,7 +3,7 @@
 This module holds no stencil arithmetic: it only draws numbers.  The paper's
 own inputs (grids "generated by STENCILGEN", Section 7) are not available, so
 these generators stand in for them with the same structure: dense grids of
-uniform values and fixed coefficient sets (Table 3 shapes), plus the size and
+uniform values and fixed coefficient sets (the shapes of Table 2), plus the size and
 arrival mixes used by the batched and served workloads.
 
 Random stream: SplitMix64 seeded with `seed`; the i-th draw (i = 0, 1, ...) is

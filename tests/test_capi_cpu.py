@@ -1,0 +1,87 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point include/ebisu.h declares, and rejects bad arguments with
+the documented status codes before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2305_07390_gb300 import ebisu
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "ebisu.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ebisu_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["ebisu_plan_create", "ebisu_run", "ebisu_batch_run", "ebisu_serve_create",
+                     "ebisu_serve_submit", "ebisu_serve_poll", "ebisu_serve_destroy", "ebisu_plan_destroy",
+                     "ebisu_status_string", "ebisu_plan_workspace_bytes"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported():
+    lib = ebisu.lib()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+    # and the binding knows every one of them
+    assert set(declared_functions()) <= set(ebisu.SIGNATURES)
+
+
+def test_status_strings():
+    for code in range(9):
+        assert ebisu.status_string(code)
+    assert ebisu.status_string(999) == "unknown status"
+
+
+@pytest.mark.parametrize("args,code", [
+    ((1, (10,), 0, 1), ebisu.ERR_INVALID_ARG),          # ndim
+    ((2, (10, 10), 5, 1), ebisu.ERR_INVALID_ARG),       # shape
+    ((2, (10, 10), 0, 4), ebisu.ERR_UNSUPPORTED),       # star radius > 3
+    ((2, (10, 10), 1, 3), ebisu.ERR_UNSUPPORTED),       # box radius > 2
+    ((2, (0, 10), 0, 1), ebisu.ERR_INVALID_ARG),        # empty axis
+    ((2, (10, 10), 0, 0), ebisu.ERR_INVALID_ARG),       # radius 0
+])
+def test_plan_create_errors(args, code):
+    ndim, dims, shape, r = args
+    with pytest.raises(ebisu.EbisuError) as ei:
+        ebisu.ebisu_plan_create(ndim, dims, shape, r, [0.1] * 125, 0, 0)
+    assert ei.value.code == code
+
+
+def test_periodic_too_small_is_unsupported():
+    with pytest.raises(ebisu.EbisuError) as ei:
+        ebisu.ebisu_plan_create(2, (6, 40), 0, 3, [0.1] * 13, 0, 1)
+    assert ei.value.code == ebisu.ERR_UNSUPPORTED
+
+
+def test_plan_defaults_and_params():
+    p = ebisu.Plan(2, (8192, 8192), 0, 1, [0.2] * 5, ebisu.F64, ebisu.DIRICHLET)
+    q = p.params()
+    assert q.depth >= 1 and q.tile_x >= 1
+    assert p.workspace_bytes() >= 8192 * 8192 * 8
+    pred, bound, valid = p.model()
+    assert pred > 0 and 0 < valid <= 1
+    # FP64 on this device is FP-pipe bound; the model keeps depth small
+    assert bound == "fp"
+    with pytest.raises(ebisu.EbisuError):
+        p.set_params(depth=0)
+    with pytest.raises(ebisu.EbisuError):
+        p.set_params(tile_x=4096, depth=64)  # plane too large for the kernel
+
+
+def test_run_argument_errors_need_no_device():
+    p = ebisu.Plan(2, (16, 16), 0, 1, [0.2] * 5, ebisu.F64, ebisu.DIRICHLET)
+    lib = ebisu.lib()
+    assert lib.ebisu_run(p.h, None, None, 1, None, None) == ebisu.ERR_INVALID_ARG
+    assert lib.ebisu_run(p.h, ctypes.c_void_p(256), ctypes.c_void_p(512), -1, ctypes.c_void_p(1024),
+                         None) == ebisu.ERR_INVALID_ARG
+    # unaligned workspace
+    assert lib.ebisu_run(p.h, ctypes.c_void_p(256), ctypes.c_void_p(512), 1, ctypes.c_void_p(1000),
+                         None) == ebisu.ERR_INVALID_ARG

@@ -52,7 +52,7 @@ def independent_offsets(ndim, shape, r):
     (2, synth.BOX, 1, 9), (2, synth.BOX, 2, 25),
     (3, synth.STAR, 1, 7), (3, synth.STAR, 2, 13), (3, synth.BOX, 1, 27), (3, synth.BOX, 2, 125)])
 def test_offset_counts_match_table3(ndim, shape, r, npts):
-    # Table 3 (benchmarks): j2d5pt, j2d9pt, 2D r3 star, j2d9pt-gol, j2d25pt,
+    # Table 2 (benchmarks): j2d5pt, j2d9pt, 2D r3 star, j2d9pt-gol, j2d25pt,
     # j3d7pt, j3d13pt, j3d27pt and the 125-point box.
     offs = oracle.offsets(ndim, shape, r)
     assert offs.shape == (npts, 3)
