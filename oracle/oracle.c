@@ -6,7 +6,7 @@
  * leg do.  It shares no code, header or table with the CUDA path.
  *
  * What it computes.  The paper's stencils (Section 2.1, Listings 1-3, and the
- * benchmark list of Table 3) are Jacobi updates: every interior cell of the new
+ * benchmark list of Table 2) are Jacobi updates: every interior cell of the new
  * time level is a fixed weighted sum of the previous level at fixed offsets,
  *
  *     u_s(x) = sum_k c_k * u_{s-1}(x + o_k),      s = 1 .. T.
