@@ -26,6 +26,7 @@ using namespace ebisu;
 
 struct BatchGroup {
     const ebisu_plan_s* kind = nullptr;  // representative plan (kernel type)
+    int variant = 0;                     // kernel build (same for all members)
     std::vector<int> members;            // problem indices
     size_t ctl_off = 0, items_off = 0;
     int64_t nitems = 0;
@@ -53,10 +54,11 @@ struct ebisu_batch_s {
 namespace {
 
 struct Key {
-    int ndim, shape, radius, dtype;
+    int ndim, shape, radius, dtype, variant;
     bool operator<(const Key& o) const
     {
-        return std::tie(ndim, shape, radius, dtype) < std::tie(o.ndim, o.shape, o.radius, o.dtype);
+        return std::tie(ndim, shape, radius, dtype, variant) <
+               std::tie(o.ndim, o.shape, o.radius, o.dtype, o.variant);
     }
 };
 
@@ -83,12 +85,13 @@ int layout(ebisu_batch_s* b)
         const ebisu_plan_s* p = &b->plans[i];
         if (p->prm.variant != 0) return EBISU_ERR_UNSUPPORTED;
         if (b->steps[i] <= 0) continue;  // zero steps: plain copy, no kernel
-        Key k{p->ndim, p->shape, p->radius, p->dtype};
+        Key k{p->ndim, p->shape, p->radius, p->dtype, kernel_variant(p->dtype, p->prm.ctas_per_sm)};
         auto it = gid.find(k);
         if (it == gid.end()) {
             it = gid.emplace(k, (int)b->groups.size()).first;
             b->groups.emplace_back();
             b->groups.back().kind = p;
+            b->groups.back().variant = k.variant;
         }
         b->groups[it->second].members.push_back(i);
     }
@@ -131,7 +134,7 @@ int layout(ebisu_batch_s* b)
         for (int m : g.members) {
             const ebisu_plan_s* p = &b->plans[m];
             const int d = (int)std::min<int64_t>(p->prm.depth, b->steps[m]);
-            const size_t slots = (size_t)ring_q0(p->radius) + (size_t)(d - 1) * ring_q(p->radius);
+            const size_t slots = (size_t)ring_q0(p->radius, p->ndim, g.variant) + (size_t)(d - 1) * ring_q(p->radius);
             need = std::max(need, slots * (size_t)g.plane_cap * p->esize);
         }
         g.smem = need;
@@ -229,7 +232,7 @@ int ebisu_batch_create(int n, const ebisu_plan_t* plans, const void* const* in, 
     for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
         BatchGroup& g = b->groups[gi];
         int occ = 0;
-        e = tb_occupancy(g.kind, g.smem, &occ);
+        e = tb_occupancy(g.kind, g.variant, g.smem, &occ);
         if (e != cudaSuccess) break;
         if (occ < 1) {
             delete b;
@@ -279,7 +282,7 @@ int ebisu_batch_launch(ebisu_batch_t b, void* stream)
         prm.ctl = (Control*)(ws + g.ctl_off);
         prm.timeout_ns = wait_timeout_ns();
         prm.smem_plane = g.plane_cap;
-        e = tb_launch(g.kind, prm, g.grid, g.smem, st);
+        e = tb_launch(g.kind, g.variant, prm, g.grid, g.smem, st);
     }
     if (e != cudaSuccess) return fail_cuda(e);
     return EBISU_OK;

@@ -25,9 +25,9 @@ struct PadParams {
 };
 
 #define EBISU_DECLARE_DTYPE_ENTRY(NAME)                                                          \
-    cudaError_t tb_launch_##NAME(int d, int s, int r, const TBParams& p, int g, size_t sm,       \
+    cudaError_t tb_launch_##NAME(int d, int s, int r, int v, const TBParams& p, int g, size_t sm, \
                                  cudaStream_t st);                                               \
-    cudaError_t tb_occupancy_##NAME(int d, int s, int r, size_t sm, int* b);                     \
+    cudaError_t tb_occupancy_##NAME(int d, int s, int r, int v, size_t sm, int* b);              \
     cudaError_t naive_launch_##NAME(int d, int s, int r, const void* a, void* b,                 \
                                     const NaiveParams& p, cudaStream_t st);                      \
     cudaError_t pad_copy_##NAME(const void* s, void* d0, void* d1, const PadParams& p,           \

@@ -2,6 +2,9 @@
 // every kernel template over (ndim, shape, radius) for one storage type.
 // Included once per storage type by kern_f64.cu / kern_f32.cu / kern_bf16.cu.
 #pragma once
+#include <mutex>
+#include <unordered_map>
+
 #include "dispatch.h"
 #include "tb_kernel.cuh"
 
@@ -150,16 +153,33 @@ __global__ void __launch_bounds__(kRedThreads) reduce_partial_kernel(const T* __
     X(3, kStar, 1) X(3, kStar, 2) X(3, kStar, 3) X(3, kBox, 1) X(3, kBox, 2)
 
 constexpr int kTBThreads = 256;
-constexpr int kTBILP = 4;
-constexpr int kTBPrefetch = 4;
 constexpr int kTBStage = 16;
+constexpr int kTBILP = 4;
+
+// Two builds of the blocked kernel per stencil:
+//   variant 0: up to 128 registers (2 resident CTAs), deep prefetch
+//              (4 planes in 2D, 2 in 3D);
+//   variant 1 (FP64 only): up to 64 registers and 2 planes of prefetch, so
+//              that 4 CTAs fit on an SM.  The FP64 pipe only stays busy when
+//              enough warps are resident to cover the per-plane barrier.
+// tb_variant_prefetch() must agree with prefetch_planes() on the host.
+template <class T, int DIM, int SHAPE, int R, int V>
+struct TBInst {
+    static constexpr int PF = (V == 1) ? 2 : (DIM == 3 ? 2 : 4);
+    static constexpr int MINB = (V == 1) ? 4 : 2;
+    static const void* ptr() { return (const void*)&tb_kernel<T, DIM, SHAPE, R, kTBThreads, kTBILP, PF, kTBStage, MINB>; }
+};
 
 template <class T>
-static const void* tb_kernel_ptr(int dim, int shape, int r)
+static const void* tb_kernel_ptr(int dim, int shape, int r, int variant)
 {
 #define X(D_, S_, R_) \
-    if (dim == D_ && shape == S_ && r == R_) \
-        return (const void*)&tb_kernel<T, D_, S_, R_, kTBThreads, kTBILP, kTBPrefetch, kTBStage>;
+    if (dim == D_ && shape == S_ && r == R_) { \
+        if constexpr (sizeof(T) == 8) { \
+            if (variant == 1) return TBInst<T, D_, S_, R_, 1>::ptr(); \
+        } \
+        return TBInst<T, D_, S_, R_, 0>::ptr(); \
+    }
     EBISU_FOR_EACH_STENCIL(X)
 #undef X
     return nullptr;
@@ -175,24 +195,39 @@ static const void* naive_kernel_ptr(int dim, int shape, int r)
     return nullptr;
 }
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than what was set before, so that launches inside a stream capture make no
+// attribute calls once a warm-up launch has set the limit.
+static cudaError_t ensure_smem_limit(const void* k, size_t smem)
+{
+    static std::mutex mu;
+    static std::unordered_map<const void*, size_t> limit;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[k];
+    if (smem <= cur) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) cur = smem;
+    return e;
+}
+
 template <class T>
-static cudaError_t tb_launch_t(int dim, int shape, int r, const TBParams& p, int grid, size_t smem,
+static cudaError_t tb_launch_t(int dim, int shape, int r, int variant, const TBParams& p, int grid, size_t smem,
                                cudaStream_t st)
 {
-    const void* k = tb_kernel_ptr<T>(dim, shape, r);
+    const void* k = tb_kernel_ptr<T>(dim, shape, r, variant);
     if (!k) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&p};
     return cudaLaunchKernel(k, dim3(grid), dim3(kTBThreads), args, smem, st);
 }
 
 template <class T>
-static cudaError_t tb_occupancy_t(int dim, int shape, int r, size_t smem, int* blocks)
+static cudaError_t tb_occupancy_t(int dim, int shape, int r, int variant, size_t smem, int* blocks)
 {
-    const void* k = tb_kernel_ptr<T>(dim, shape, r);
+    const void* k = tb_kernel_ptr<T>(dim, shape, r, variant);
     if (!k) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = ensure_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kTBThreads, smem);
 }
@@ -244,14 +279,14 @@ static cudaError_t reduce_partial_t(const void* a, const void* b, double* part, 
 
 #define EBISU_DEFINE_DTYPE_ENTRY(T, NAME)                                                        \
     namespace ebisu {                                                                            \
-    cudaError_t tb_launch_##NAME(int d, int s, int r, const TBParams& p, int g, size_t sm,       \
+    cudaError_t tb_launch_##NAME(int d, int s, int r, int v, const TBParams& p, int g, size_t sm, \
                                  cudaStream_t st)                                                \
     {                                                                                            \
-        return tb_launch_t<T>(d, s, r, p, g, sm, st);                                            \
+        return tb_launch_t<T>(d, s, r, v, p, g, sm, st);                                         \
     }                                                                                            \
-    cudaError_t tb_occupancy_##NAME(int d, int s, int r, size_t sm, int* b)                      \
+    cudaError_t tb_occupancy_##NAME(int d, int s, int r, int v, size_t sm, int* b)               \
     {                                                                                            \
-        return tb_occupancy_t<T>(d, s, r, sm, b);                                                \
+        return tb_occupancy_t<T>(d, s, r, v, sm, b);                                             \
     }                                                                                            \
     cudaError_t naive_launch_##NAME(int d, int s, int r, const void* a, void* b,                 \
                                     const NaiveParams& p, cudaStream_t st)                       \

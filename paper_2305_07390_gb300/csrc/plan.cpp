@@ -64,7 +64,7 @@ int64_t wait_timeout_ns()
 }
 
 int ring_q(int radius) { return 2 * radius + 2; }
-int ring_q0(int radius) { return 2 * radius + 1 + kPrefetch; }
+int ring_q0(int radius, int ndim, int variant) { return 2 * radius + 1 + prefetch_planes(ndim, variant); }
 
 // largest level-0 region of any tile: (E1, E2), unpadded
 static void max_plane(const ebisu_plan_s* p, const ebisu_params& q, int64_t* e1, int64_t* e2)
@@ -93,7 +93,8 @@ int64_t plane_capacity(const ebisu_plan_s* p, const ebisu_params& q)
 
 size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q)
 {
-    const size_t slots = (size_t)ring_q0(p->radius) + (size_t)(q.depth - 1) * ring_q(p->radius);
+    const size_t slots = (size_t)ring_q0(p->radius, p->ndim, kernel_variant(p->dtype, q.ctas_per_sm)) +
+                         (size_t)(q.depth - 1) * ring_q(p->radius);
     return slots * (size_t)plane_capacity(p, q) * p->esize;
 }
 
@@ -158,21 +159,21 @@ int64_t fill_grid_desc(const ebisu_plan_s* p, const void* in, void* out, void* w
     return nb * (int64_t)g->ntiles;
 }
 
-cudaError_t tb_launch(const ebisu_plan_s* p, const TBParams& prm, int grid, size_t smem, cudaStream_t st)
+cudaError_t tb_launch(const ebisu_plan_s* p, int v, const TBParams& prm, int grid, size_t smem, cudaStream_t st)
 {
     switch (p->dtype) {
-    case EBISU_F64: return tb_launch_f64(p->ndim, p->shape, p->radius, prm, grid, smem, st);
-    case EBISU_F32: return tb_launch_f32(p->ndim, p->shape, p->radius, prm, grid, smem, st);
-    default: return tb_launch_bf16(p->ndim, p->shape, p->radius, prm, grid, smem, st);
+    case EBISU_F64: return tb_launch_f64(p->ndim, p->shape, p->radius, v, prm, grid, smem, st);
+    case EBISU_F32: return tb_launch_f32(p->ndim, p->shape, p->radius, v, prm, grid, smem, st);
+    default: return tb_launch_bf16(p->ndim, p->shape, p->radius, v, prm, grid, smem, st);
     }
 }
 
-cudaError_t tb_occupancy(const ebisu_plan_s* p, size_t smem, int* blocks)
+cudaError_t tb_occupancy(const ebisu_plan_s* p, int v, size_t smem, int* blocks)
 {
     switch (p->dtype) {
-    case EBISU_F64: return tb_occupancy_f64(p->ndim, p->shape, p->radius, smem, blocks);
-    case EBISU_F32: return tb_occupancy_f32(p->ndim, p->shape, p->radius, smem, blocks);
-    default: return tb_occupancy_bf16(p->ndim, p->shape, p->radius, smem, blocks);
+    case EBISU_F64: return tb_occupancy_f64(p->ndim, p->shape, p->radius, v, smem, blocks);
+    case EBISU_F32: return tb_occupancy_f32(p->ndim, p->shape, p->radius, v, smem, blocks);
+    default: return tb_occupancy_bf16(p->ndim, p->shape, p->radius, v, smem, blocks);
     }
 }
 
@@ -419,14 +420,15 @@ static int run_common(ebisu_plan_t p, const void* in, void* out, int64_t steps, 
     qd.depth = d;
     prm.smem_plane = (int32_t)plane_capacity(p, qd);
     const size_t smem = tb_smem_bytes(p, qd);
+    const int variant = kernel_variant(p->dtype, q.ctas_per_sm);
     int occ = 0;
-    e = tb_occupancy(p, smem, &occ);
+    e = tb_occupancy(p, variant, smem, &occ);
     if (e != cudaSuccess) return fail_cuda(e);
     if (occ < 1) return EBISU_ERR_UNSUPPORTED;
     const DeviceInfo& dv = device_info();
     int64_t grid = (int64_t)std::min(occ, q.ctas_per_sm) * dv.sms;
     grid = std::min<int64_t>(grid, prm.nitems);
-    e = tb_launch(p, prm, (int)grid, smem, st);
+    e = tb_launch(p, variant, prm, (int)grid, smem, st);
     if (e != cudaSuccess) return fail_cuda(e);
     return EBISU_OK;
 }

@@ -28,7 +28,11 @@ namespace ebisu {
 
 constexpr int kThreads = 256;      // threads per CTA of the blocked kernel
 constexpr int kStagePerThread = 16; // register-staged plane elements per thread
-constexpr int kPrefetch = 4;        // input planes in flight (cp.async)
+// Build of the blocked kernel a parameter set runs (see kernels_impl.cuh):
+// FP64 with 3 or more CTAs per SM uses the 64-register, 2-plane-prefetch build.
+inline int kernel_variant(int dtype, int ctas_per_sm) { return (dtype == EBISU_F64 && ctas_per_sm >= 3) ? 1 : 0; }
+// Input planes in flight (cp.async) of a build.
+inline int prefetch_planes(int ndim, int variant) { return (variant == 1 || ndim == 3) ? 2 : 4; }
 
 struct DeviceInfo {
     int device = -1;
@@ -50,7 +54,7 @@ void set_cuda_error(cudaError_t e);
 int fail_cuda(cudaError_t e);
 
 int ring_q(int radius);   // slots of a level-1.. ring (2r+2)
-int ring_q0(int radius);  // slots of the input ring (2r+1+prefetch)
+int ring_q0(int radius, int ndim, int variant);  // slots of the input ring (2r+1+prefetch)
 // Elements per ring plane and dynamic shared memory of a parameter set.
 int64_t plane_capacity(const ebisu_plan_s* p, const ebisu_params& q);
 size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q);
@@ -65,8 +69,9 @@ double model_pp(const ebisu_plan_s* p, const ebisu_params& q, int64_t steps, int
 int64_t fill_grid_desc(const ebisu_plan_s* p, const void* in, void* out, void* wsgrid, int64_t steps,
                        bool in_copied_to_ws, GridDesc* g);
 
-cudaError_t tb_launch(const ebisu_plan_s* p, const TBParams& prm, int grid, size_t smem, cudaStream_t st);
-cudaError_t tb_occupancy(const ebisu_plan_s* p, size_t smem, int* blocks);
+cudaError_t tb_launch(const ebisu_plan_s* p, int variant, const TBParams& prm, int grid, size_t smem,
+                      cudaStream_t st);
+cudaError_t tb_occupancy(const ebisu_plan_s* p, int variant, size_t smem, int* blocks);
 cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, cudaStream_t st);
 cudaError_t pad_copy(const ebisu_plan_s* p, const void* src, void* d0, void* d1, cudaStream_t st);
 

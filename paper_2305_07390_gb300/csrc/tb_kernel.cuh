@@ -30,6 +30,8 @@
 //    from global memory), so no intermediate level ever computes a pad cell.
 //    Periodic neighbours wrap when level 0 is loaded.
 #pragma once
+#include <type_traits>
+
 #include "common.h"
 #include "stencil.cuh"
 
@@ -64,8 +66,8 @@ __device__ __forceinline__ int fast_div(int i, float inv_d, int d)
 
 enum { kLoadElem = 0, kLoadPairs = 1, kLoadStaged = 2 };
 
-template <class T, int DIM, int SHAPE, int R, int NT, int ILP, int PF, int STG>
-__global__ void __launch_bounds__(NT, 2) tb_kernel(const __grid_constant__ TBParams prm)
+template <class T, int DIM, int SHAPE, int R, int NT, int ILP, int PF, int STG, int MINB>
+__global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TBParams prm)
 {
     using St = Stencil<DIM, SHAPE, R>;
     using D = DT<T>;
@@ -74,7 +76,8 @@ __global__ void __launch_bounds__(NT, 2) tb_kernel(const __grid_constant__ TBPar
     constexpr int Q0 = RingGeom<R, PF>::Q0;
     constexpr int Q = RingGeom<R, PF>::Q;
     constexpr int RP1 = St::kRP1;
-    constexpr bool kCoefRegs = (P <= 32);
+    // coefficients in registers when they are few, else broadcast from shared memory
+    constexpr bool kCoefRegs = (P * sizeof(typename DT<T>::C) <= (MINB >= 4 ? 40 : 128));
     constexpr auto OFF = St::kOff;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -344,47 +347,71 @@ __global__ void __launch_bounds__(NT, 2) tb_kernel(const __grid_constant__ TBPar
                 const int64_t pk = ps + k - R;
                 base[k] = ring_plane(s - 1, pk) + ((s == 1) ? pshift(pk) : 0);
             }
-            for (int i0 = tid; i0 < cnt; i0 += ILP * NT) {
-                int off[ILP], rd[ILP], q1v[ILP], q2v[ILP];
-                bool val[ILP], hal[ILP];
+            // cell index i -> (q1, q2) of this level's region
+            auto cell = [&](int i, int& q1, int& q2) {
+                const int r1 = (DIM == 3) ? fast_div(i, invR2, R2) : 0;
+                q1 = l1 + r1;
+                q2 = l2 + (i - r1 * R2);
+            };
+            auto is_pad = [&](int q1, int q2) -> bool {
+                return edge && (q1 < 0 || q1 >= n1 || q2 < 0 || q2 >= n2);
+            };
+            // U cells per thread, slots i0, i0 + NT, ... (U is compile-time)
+            auto group = [&](auto UC, int i0) {
+                constexpr int U = decltype(UC)::value;
+                int rd[U];
 #pragma unroll
-                for (int u = 0; u < ILP; ++u) {
+                for (int u = 0; u < U; ++u) {
                     const int i = i0 + u * NT;
-                    val[u] = i < cnt;
-                    const int ii = val[u] ? i : 0;
-                    const int r1 = (DIM == 3) ? fast_div(ii, invR2, R2) : 0;
-                    const int q1 = l1 + r1, q2 = l2 + (ii - r1 * R2);
-                    q1v[u] = q1;
-                    q2v[u] = q2;
-                    hal[u] = edge && (q1 < 0 || q1 >= n1 || q2 < 0 || q2 >= n2);
-                    off[u] = (q1 - lo01) * E2p + (q2 - lo02);
-                    rd[u] = (val[u] && !hal[u]) ? off[u] : safe_off;
+                    int q1, q2;
+                    cell(i < cnt ? i : 0, q1, q2);
+                    const bool comp = (i < cnt) && !is_pad(q1, q2);
+                    rd[u] = comp ? (q1 - lo01) * E2p + (q2 - lo02) : safe_off;
                 }
-                C acc[ILP];
+                C acc[U];
                 {
                     const C c0 = kCoefRegs ? cr[0] : s_coef[0];
                     const T* bp = base[OFF.ds[0] + R] + OFF.d1[0] * E2p + OFF.d2[0];
 #pragma unroll
-                    for (int u = 0; u < ILP; ++u) acc[u] = D::mul(c0, D::widen(bp[rd[u]]));
+                    for (int u = 0; u < U; ++u) acc[u] = D::mul(c0, D::widen(bp[rd[u]]));
                 }
 #pragma unroll
                 for (int k = 1; k < P; ++k) {
                     const C ck = kCoefRegs ? cr[k] : s_coef[k];
                     const T* bp = base[OFF.ds[k] + R] + OFF.d1[k] * E2p + OFF.d2[k];
 #pragma unroll
-                    for (int u = 0; u < ILP; ++u) acc[u] = D::fma(ck, D::widen(bp[rd[u]]), acc[u]);
+                    for (int u = 0; u < U; ++u) acc[u] = D::fma(ck, D::widen(bp[rd[u]]), acc[u]);
                 }
 #pragma unroll
-                for (int u = 0; u < ILP; ++u) {
-                    if (!val[u]) continue;
-                    T v = D::narrow(acc[u]);
-                    if (hal[u]) v = self[off[u]];
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + u * NT;
+                    if (i >= cnt) continue;
+                    int q1, q2;
+                    cell(i, q1, q2);
+                    const int off = (q1 - lo01) * E2p + (q2 - lo02);
+                    const bool pc = is_pad(q1, q2);
+                    const T v = pc ? self[off] : D::narrow(acc[u]);
                     if (to_global) {
-                        if (!hal[u]) gout[ginplane(q1v[u], q2v[u])] = v;
+                        if (!pc) gout[ginplane(q1, q2)] = v;
                     } else {
-                        outp[off[u]] = v;
+                        outp[off] = v;
                     }
                 }
+            };
+            static_assert(ILP == 4, "slot dispatch below assumes ILP = 4");
+            for (int i0 = tid; i0 < cnt; i0 += ILP * NT) {
+                // slots that hold at least one cell of this warp (warp-uniform),
+                // so a short last pass issues no FMAs for empty slots
+                const int wbase = i0 - (tid & 31);
+                const int uw = min(ILP, (cnt - wbase + NT - 1) / NT);
+                if (uw >= 4)
+                    group(std::integral_constant<int, 4>{}, i0);
+                else if (uw == 3)
+                    group(std::integral_constant<int, 3>{}, i0);
+                else if (uw == 2)
+                    group(std::integral_constant<int, 2>{}, i0);
+                else
+                    group(std::integral_constant<int, 1>{}, i0);
             }
         };
 

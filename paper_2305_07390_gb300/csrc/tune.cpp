@@ -114,7 +114,12 @@ double model_pp(const ebisu_plan_s* p, const ebisu_params& q, int64_t steps, int
     tmp.prm.depth = t;
     fill_grid_desc(&tmp, nullptr, nullptr, nullptr, std::max<int64_t>(steps, 1), false, &g);
     double useful = 0, loaded = 0;
-    const double computed = trapezoid_cells(p, g, t, &useful, &loaded);
+    double computed = trapezoid_cells(p, g, t, &useful, &loaded);
+    const double vsm = useful / computed;
+    // Partial warps: each level-plane region is processed in warp-wide
+    // slots; on average half a warp of a region's last slot is empty.
+    const double region = (double)g.tile[1] * g.tile[2];
+    computed *= 1.0 + 16.0 / std::max(region, 32.0);
     const double S = (double)p->esize;
     const double cells = (double)g.n[0] * g.n[1] * g.n[2];
     const double thr = (p->dtype == EBISU_F64) ? dv.f64 : dv.f32;
@@ -125,15 +130,26 @@ double model_pp(const ebisu_plan_s* p, const ebisu_params& q, int64_t steps, int
     int b = 0;
     if (T == Tsm) b = 1;
     if (T == Tcmp) b = 2;
+    // Resident CTAs per SM: shared memory and the build's register cap.
+    const size_t smem = tb_smem_bytes(p, tmp.prm) + 4096;
+    const int variant = kernel_variant(p->dtype, q.ctas_per_sm);
+    const int reg_cap = (variant == 1) ? 4 : 2;
+    const int fit = (int)std::max<size_t>(1, dv.smem_per_sm / std::max<size_t>(smem, 1));
+    const int res = std::max(1, std::min(std::min(q.ctas_per_sm, fit), reg_cap));
+    // The one barrier per streamed plane idles the FP pipe unless other
+    // warps are resident; measured on this part: 8 warps/SM keep it ~60%
+    // busy, 16 ~85%, 32 ~95% (2D FP64 sweeps).
+    const double warps = 8.0 * res;
+    const double eff = 1.0 - 0.4 * std::exp(-(warps - 8.0) / 8.0);
+    T /= eff;
     // wave quantisation of one temporal block over the resident CTAs
-    const double ctas = (double)dv.sms * std::max(1, q.ctas_per_sm);
+    const double ctas = (double)dv.sms * res;
     const double waves = std::ceil((double)g.ntiles / ctas);
     const double vwave = (double)g.ntiles / (waves * ctas);
     // one temporal block (stretched by the wave quantisation) plus one
     // dependency wait between blocks: Eq. 11 with n = 1 (lazy streaming)
     const double Tblock = T / vwave;
     const double vsync = Tblock / (Tblock + dv.barrier_s);
-    const double vsm = useful / computed;
     if (bound) *bound = b;
     if (valid) *valid = vsm;
     const double P = useful / T;  // cell updates per second at the bound
@@ -152,17 +168,18 @@ int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, dou
     std::vector<int> depths = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16};
     std::vector<int> txs, tys;
     if (p->ndim == 2) {
-        for (int x : {256, 512, 768, 1024, 1536, 2048, 3072, 4000}) push_unique(txs, (int)std::min<int64_t>(x, p->n[2]));
+        for (int x : {512, 1024, 1536, 2048, 3072, 4000}) push_unique(txs, (int)std::min<int64_t>(x, p->n[2]));
         tys.push_back(1);
     } else {
-        for (int x : {16, 32, 48, 64, 96, 128}) push_unique(txs, (int)std::min<int64_t>(x, p->n[2]));
-        for (int y : {8, 16, 32, 48, 64}) push_unique(tys, (int)std::min<int64_t>(y, p->n[1]));
+        for (int x : {32, 64, 128}) push_unique(txs, (int)std::min<int64_t>(x, p->n[2]));
+        for (int y : {8, 16, 32, 64}) push_unique(tys, (int)std::min<int64_t>(y, p->n[1]));
     }
     for (int d : depths) {
         if (d > std::max<int64_t>(steps, 1) && d != 1) continue;
         for (int tx : txs)
             for (int ty : tys)
-                for (int cps : {1, 2}) {
+                for (int cps : {1, 2, 4}) {
+                    if (cps == 4 && p->dtype != EBISU_F64) continue;
                     ebisu_params q;
                     memset(&q, 0, sizeof(q));
                     q.tile_x = tx;
@@ -172,6 +189,7 @@ int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, dou
                     q.threads = kThreads;
                     if (check_params(p, q) != EBISU_OK) continue;
                     if (cps > 1 && (tb_smem_bytes(p, q) + 4096) * cps > dv.smem_per_sm) continue;
+                    (void)0;
                     // band length along the streamed axis: enough tiles for
                     // one or two waves of resident CTAs
                     const int64_t nt2 = (p->n[2] + tx - 1) / tx;
