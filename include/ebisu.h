@@ -155,6 +155,33 @@ int ebisu_run(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
 int ebisu_run_naive(ebisu_plan_t plan, const void* in, void* out,
                     int64_t steps, void* workspace, void* stream);
 
+/* ebisu_run without a caller workspace and without any allocation.  The
+ * paper has no counterpart; this is a deployment convenience.
+ *
+ * For callers that cannot allocate device memory or hand the library a
+ * workspace: hosts that own all device memory through their own pool and
+ * forbid outside allocations, programs whose memory budget is fixed at
+ * start-up, and latency-critical loops where an allocation, which may
+ * synchronise the device, is not acceptable.
+ *
+ * The workspace is a fixed 64 MiB array inside the library (one per device,
+ * reserved when this part of the library is first loaded on that device and
+ * held until the process exits), so the plan's ebisu_plan_workspace_bytes
+ * must not exceed 64 MiB: about 8.3 M FP64, 16.7 M FP32 or 33 M BF16 stored
+ * cells (a 2048 x 2048 FP64 grid fits).  Larger plans return
+ * EBISU_ERR_UNSUPPORTED and nothing is enqueued.
+ *   plan, in, out, steps, stream : as for ebisu_run (in == out allowed).
+ *   wait : 0 = enqueue and return; nonzero = also wait for the stream and
+ *          return the kernels' status (as ebisu_sync would).
+ * The first call on a device looks up the array's device address (a host
+ * call, done once per device with that device current).  Every call on a
+ * device uses the same array, and the array keeps what the last call left
+ * in it; each call resets the part that must start at zero (the control
+ * block) itself.  Calls whose work overlaps on the GPU, on different streams
+ * or threads, race on the array: serialise them. */
+int ebisu_run_static(ebisu_plan_t plan, const void* in, void* out,
+                     int64_t steps, void* stream, int wait);
+
 /* Wait for `stream`, then read and clear the status word that kernels of
  * the last run on `workspace` left there.  Returns EBISU_OK, EBISU_ERR_CUDA
  * (a CUDA error, whose text ebisu_last_cuda_error gives) or the kernel's

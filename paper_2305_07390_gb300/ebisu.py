@@ -79,6 +79,7 @@ SIGNATURES = {
     "ebisu_plan_workspace_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "ebisu_run": (_I, [_P, _P, _P, _I64, _P, _P]),
     "ebisu_run_naive": (_I, [_P, _P, _P, _I64, _P, _P]),
+    "ebisu_run_static": (_I, [_P, _P, _P, _I64, _P, _I]),
     "ebisu_sync": (_I, [_P, _P]),
     "ebisu_plan_tune": (_I, [_P, _P, _P, _I64, _P, _I, ctypes.POINTER(_D), _P]),
     "ebisu_plan_model": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
