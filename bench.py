@@ -133,6 +133,144 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_case(args):
+    """One solve of one stencil (for ncu captures of a single kernel)."""
+    import torch
+    from paper_2305_07390_gb300 import ebisu, synth
+    nd, shp, r = args.case.split(":")
+    nd, r = int(nd), int(r)
+    shape = 0 if shp == "star" else 1
+    dt = {"f64": ebisu.F64, "f32": ebisu.F32, "bf16": ebisu.BF16}[args.dtype]
+    dims = (args.n,) * nd
+    g, c = synth.problem(nd, dims, shape, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED)
+    plan = ebisu.Plan(nd, dims, shape, r, c, dt, ebisu.DIRICHLET)
+    if args.params:
+        plan.set_params(**{k: int(v) for k, v in (kv.split("=") for kv in args.params.split(","))})
+    x = torch.from_numpy(g).to(ebisu.torch_dtype(dt)).cuda()
+    y = torch.empty_like(x)
+    ws = plan.workspace()
+    plan.run(x, y, args.solve_steps, ws, naive=args.naive)
+    rc = plan.sync(ws)
+    assert rc == 0, ebisu.status_string(rc)
+    print(json.dumps({"case": args.case, "n": args.n, "dtype": args.dtype, "steps": args.solve_steps,
+                      "params": plan.params().as_dict(), "naive": args.naive}))
+
+
+def run_batch(args):
+    """512 uneven 2D 9-point box grids (sides log-uniform in [256, 4096],
+    aspect in [0.25, 4], 16-512 steps) in one persistent launch per dtype,
+    against the same grids run one after another with ebisu_run."""
+    import numpy as np
+    import torch
+    from paper_2305_07390_gb300 import ebisu, synth
+    mix = synth.batch_mix(512)
+    out = {"workload": "batch: 512 uneven 2D 9-point box grids, Dirichlet, tiles and depth from the autotuner's "
+                       "cost model", "n_grids": len(mix), "cells": int(sum(a * b for a, b, _ in mix)),
+           "cell_updates": int(sum(a * b * s for a, b, s in mix)), "by_dtype": {}}
+    stream = torch.cuda.current_stream()
+    for dname, dt in (("f64", ebisu.F64), ("f32", ebisu.F32), ("bf16", ebisu.BF16)):
+        plans, xs, ys, steps = [], [], [], []
+        for i, (ny, nx, st) in enumerate(mix):
+            g, c = synth.problem(2, (ny, nx), synth.BOX, 1, synth.DIRICHLET, seed=synth.DEFAULT_SEED + i)
+            plans.append(ebisu.Plan(2, (ny, nx), ebisu.BOX, 1, c, dt, ebisu.DIRICHLET))
+            xs.append(torch.from_numpy(g).to(ebisu.torch_dtype(dt)).cuda())
+            ys.append(torch.empty_like(xs[-1]))
+            steps.append(st)
+        ws = torch.empty(ebisu.batch_workspace_bytes(plans, steps), dtype=torch.uint8, device="cuda")
+        b = ebisu.Batch(plans, xs, ys, steps, ws)
+        for _ in range(args.warmup):
+            b.launch()
+        torch.cuda.synchronize()
+        assert b.sync() == 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_batch = e0.elapsed_time(e1) / args.steps
+        # the same grids one after another (one launch each)
+        wss = [p.workspace() for p in plans[:1]]
+        big = max(p.workspace_bytes() for p in plans)
+        wsa = torch.empty(big, dtype=torch.uint8, device="cuda")
+        e0.record(stream)
+        for p, x, y, st in zip(plans, xs, ys, steps):
+            p.run(x, y, st, wsa)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_alone = e0.elapsed_time(e1)
+        out["by_dtype"][dname] = {"ms_batched": ms_batch, "ms_one_by_one": ms_alone,
+                                  "cell_updates_per_s": out["cell_updates"] / (ms_batch * 1e-3),
+                                  "batching_speedup": ms_alone / ms_batch}
+        del plans, xs, ys, ws, b, wsa
+        torch.cuda.empty_cache()
+    f64 = out["by_dtype"]["f64"]["ms_batched"]
+    for dname in ("f32", "bf16"):
+        out["by_dtype"][dname]["speedup_vs_f64"] = f64 / out["by_dtype"][dname]["ms_batched"]
+    print(json.dumps(out), flush=True)
+
+
+def run_serve(args):
+    """Open-loop Poisson arrivals through the serving loop (continuous
+    batching, 120 GB budget).  Inputs are prefixes of one preallocated buffer
+    per (ndim, dtype) and outputs share one buffer per (ndim, dtype): results
+    are not kept (their correctness is covered by the test suite); this
+    measures admission, queueing and latency."""
+    import numpy as np
+    import torch
+    from paper_2305_07390_gb300 import ebisu, synth
+    budget = 120 << 30
+    srv = ebisu.Server(hbm_budget=budget, max_slots=4)
+    srv.set_max_queue(256)
+    bufs = {}
+    for nd, side in ((2, 8192 + 2), (3, 512 + 2)):
+        for dname, dt in (("f64", ebisu.F64), ("f32", ebisu.F32)):
+            n = side ** nd
+            x = torch.from_numpy(synth.uniform01(synth.DEFAULT_SEED, 0, n)).to(ebisu.torch_dtype(dt)).cuda()
+            bufs[(nd, dname)] = (x, torch.empty_like(x))
+    coef = {}
+    results = []
+    for rate in [float(v) for v in args.serve_rates.split(",")]:
+        reqs = synth.serve_mix(rate, args.serve_seconds)
+        tickets = []
+        rejected = 0
+        t0 = time.perf_counter()
+        for rq in reqs:
+            while time.perf_counter() - t0 < rq["t"]:
+                time.sleep(min(0.0005, max(0.0, rq["t"] - (time.perf_counter() - t0))))
+            key = (rq["ndim"], rq["shape"])
+            if key not in coef:
+                coef[key] = synth.coefficients(rq["ndim"], rq["shape"], 1, rq["dims"], synth.DIRICHLET)
+            dt = ebisu.F64 if rq["dtype"] == "f64" else ebisu.F32
+            plan = ebisu.Plan(rq["ndim"], rq["dims"], rq["shape"], 1, coef[key], dt, ebisu.DIRICHLET)
+            x, y = bufs[(rq["ndim"], rq["dtype"])]
+            rc, t = srv.try_submit(plan, x, y, rq["steps"])
+            if rc == ebisu.OK:
+                tickets.append((t, rq))
+            else:
+                rejected += 1
+        t_arrive = time.perf_counter() - t0
+        lat = []
+        upd = 0
+        for t, rq in tickets:
+            lat.append(srv.wait(t, timeout_s=600.0))
+            upd += int(np.prod(rq["dims"])) * rq["steps"]
+        t_all = time.perf_counter() - t0
+        lat.sort()
+        q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
+        st = srv.stats()
+        results.append({"rate_hz": rate, "offered": len(reqs), "completed": len(tickets), "rejected": rejected,
+                        "p50_s": q(0.50), "p99_s": q(0.99), "max_s": lat[-1] if lat else None,
+                        "throughput_cell_updates_per_s": upd / t_all, "arrival_window_s": t_arrive,
+                        "drain_s": t_all - t_arrive, "peak_bytes": st["peak_bytes"]})
+        print(json.dumps(results[-1]), flush=True)
+    srv.close()
+    print(json.dumps({"workload": "serve: Poisson arrivals, 50% 2D (256^2-8192^2, 5pt star / 9pt box), 50% 3D "
+                                  "(64^3-512^3, 7pt star / 27pt box), FP64/FP32, 10-1000 steps, 120 GB budget, "
+                                  "queue limit 256, 4 lanes", "seconds_per_rate": args.serve_seconds,
+                      "rates": results}), flush=True)
+
+
 def cpu_baseline(budget_s=15.0):
     """Oracle cell-updates/s on the host, bounded to ~budget_s of CPU work:
     the same number of Jacobi steps of every stencil of the set on the full
@@ -167,8 +305,26 @@ def main():
     ap.add_argument("--impl", default="ebisu", choices=["ebisu", "reference"])
     ap.add_argument("--solve-steps", type=int, default=SOLVE_STEPS)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
-    ap.add_argument("--tune", type=int, default=8, help="candidates the autotuner times per stencil")
+    ap.add_argument("--tune", type=int, default=16, help="candidates the autotuner times per stencil")
+    ap.add_argument("--case", default=None,
+                    help="profiling case: run one solve of 'DIM:SHAPE:R' (e.g. 2:box:2) and exit")
+    ap.add_argument("--n", type=int, default=4096, help="--case: interior extent per axis")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="--case: storage type")
+    ap.add_argument("--params", default="", help="--case: plan parameters, k=v,k=v")
+    ap.add_argument("--naive", action="store_true", help="--case: the one-step-per-launch kernel")
+    ap.add_argument("--workload", default="set", choices=["set", "batch", "serve"],
+                    help="set: the FP64 2D stencil set (default, the headline line); batch: 512 uneven "
+                         "2D 9-point box grids in one persistent launch per dtype; serve: Poisson arrivals "
+                         "through the serving loop")
+    ap.add_argument("--serve-rates", default="5,10,20,50,100,200,500,1000,2000")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

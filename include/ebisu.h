@@ -301,7 +301,8 @@ int ebisu_serve_create(size_t hbm_budget, int max_slots, ebisu_server_t* out);
  * result to `out_dev`.  `in_dev` may be reused once ebisu_serve_poll reports
  * the request done.  The plan is copied.  Returns EBISU_ERR_BUDGET if the
  * request alone exceeds the budget and EBISU_ERR_BUSY if the queue already
- * holds 1024 waiting requests (admission control: the request is dropped).
+ * holds its limit of waiting requests (admission control: the request is
+ * dropped; the limit is 1024 unless ebisu_serve_set_max_queue changed it).
  * *ticket receives the request id. */
 int ebisu_serve_submit(ebisu_server_t s, ebisu_plan_t plan, const void* in_dev,
                        void* out_dev, int64_t steps, uint64_t* ticket);
@@ -318,6 +319,9 @@ int ebisu_serve_wait(ebisu_server_t s, uint64_t ticket, double timeout_s,
 /* Counters: stats[0] submitted, [1] completed, [2] rejected, [3] queued now,
  * [4] running now, [5] peak bytes held, [6] bytes held now. */
 int ebisu_serve_stats(ebisu_server_t s, int64_t* stats);
+
+/* Admission control: most requests that may wait in the queue (>= 1). */
+int ebisu_serve_set_max_queue(ebisu_server_t s, int max_queue);
 
 /* Cancel a request that has not started (EBISU_ERR_NOT_READY if it has). */
 int ebisu_serve_cancel(ebisu_server_t s, uint64_t ticket);

@@ -86,8 +86,9 @@ int64_t plane_capacity(const ebisu_plan_s* p, const ebisu_params& q)
 {
     int64_t e1, e2;
     max_plane(p, q, &e1, &e2);
-    // row pitch: even and >= E2 + 2 (room for the pair-load shift)
-    const int64_t pitch = (e2 + 3) & ~(int64_t)1;
+    // row pitch as the kernel lays rows out: a 4-column margin, the row, one
+    // column of pair-load shift and room for the 4-wide reads, rounded to 4
+    const int64_t pitch = (e2 + 4 + 7 + 3) & ~(int64_t)3;
     return e1 * pitch;
 }
 

@@ -58,13 +58,14 @@ struct Launch {
     void* ws = nullptr;
 };
 
-constexpr size_t kMaxQueue = 1024;
+constexpr size_t kDefaultMaxQueue = 1024;
 
 }  // namespace
 
 struct ebisu_server_s {
     size_t budget = 0;
     int max_slots = 1;
+    size_t max_queue = kDefaultMaxQueue;
     int device = 0;
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
@@ -79,11 +80,14 @@ struct ebisu_server_s {
     bool stop = false;
     std::thread th;
 
-    static size_t need_of(const ebisu_plan_s* p)
+    // Device bytes a request holds while admitted: its resident copy plus
+    // its share of a batch workspace (ping-pong buffer, control, tables).
+    static size_t need_of(ebisu_plan_t p, int64_t steps)
     {
         const size_t g = align_up((size_t)p->elems * p->esize, kAlign);
-        // resident copy + ping-pong buffer + control and work tables
-        return 2 * g + 64 * 1024;
+        size_t ws = 0;
+        if (ebisu_batch_workspace_bytes(1, &p, &steps, &ws) != EBISU_OK) ws = g + 64 * 1024;
+        return g + ws;
     }
 
     void retire_locked()
@@ -301,7 +305,7 @@ int ebisu_serve_submit(ebisu_server_t s, ebisu_plan_t plan, const void* in_dev, 
     r->in = in_dev;
     r->out = out_dev;
     r->steps = steps;
-    r->need = ebisu_server_s::need_of(plan);
+    r->need = ebisu_server_s::need_of(plan, steps);
     r->t_submit = now_s();
     std::lock_guard<std::mutex> lk(s->mu);
     ++s->submitted;
@@ -310,7 +314,7 @@ int ebisu_serve_submit(ebisu_server_t s, ebisu_plan_t plan, const void* in_dev, 
         delete r;
         return EBISU_ERR_BUDGET;
     }
-    if (s->queue.size() >= kMaxQueue || s->stop) {
+    if (s->queue.size() >= s->max_queue || s->stop) {
         ++s->rejected;
         delete r;
         return EBISU_ERR_BUSY;
@@ -361,6 +365,14 @@ int ebisu_serve_stats(ebisu_server_t s, int64_t* stats)
     stats[4] = s->nrunning;
     stats[5] = (int64_t)s->peak;
     stats[6] = (int64_t)s->held;
+    return EBISU_OK;
+}
+
+int ebisu_serve_set_max_queue(ebisu_server_t s, int max_queue)
+{
+    if (!s || max_queue < 1) return EBISU_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->max_queue = (size_t)max_queue;
     return EBISU_OK;
 }
 

@@ -54,6 +54,35 @@ struct Stencil {
         return t;
     }
     static constexpr Table kOff = make();
+
+    // Offsets sharing (ds, d1) -- one row of one plane -- are consecutive in
+    // canonical order.  Per offset k: does a new row group start at k, and
+    // the d2 range of k's row group.  Built at compile time (kernels copy it
+    // into a constexpr local, like kOff, so every lookup folds away).
+    struct RowInfo {
+        bool start[P];
+        int min_d2[P];
+        int max_d2[P];
+    };
+    static constexpr RowInfo make_rows()
+    {
+        RowInfo r{};
+        const Table t = make();
+        for (int k = 0; k < P; ++k)
+            r.start[k] = (k == 0) || t.ds[k] != t.ds[k - 1] || t.d1[k] != t.d1[k - 1];
+        for (int k = 0; k < P; ++k) {
+            int b = k;
+            while (!r.start[b]) --b;
+            int lo = t.d2[b], hi = t.d2[b];
+            for (int j = b; j < P && (j == b || !r.start[j]); ++j) {
+                lo = t.d2[j] < lo ? t.d2[j] : lo;
+                hi = t.d2[j] > hi ? t.d2[j] : hi;
+            }
+            r.min_d2[k] = lo;
+            r.max_d2[k] = hi;
+        }
+        return r;
+    }
 };
 
 // ---------------------------------------------------------------------------

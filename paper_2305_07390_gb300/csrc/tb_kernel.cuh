@@ -55,16 +55,27 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// quotient of i / d for 0 <= i < 2^22 using a float reciprocal
-__device__ __forceinline__ int fast_div(int i, float inv_d, int d)
+// Exact quotient i / d for 0 <= i < 2^22 and 1 <= d < 2^16 by a multiply and
+// a shift: with m = ceil(2^40 / d), i*m / 2^40 exceeds i/d by less than
+// i / 2^40 < 2^-18 < 1/d, so the floor is exact.  No conversion instructions.
+struct Divisor {
+    uint64_t m;
+    int d;
+};
+__device__ __forceinline__ Divisor make_divisor(int d)
 {
-    int q = (int)(((float)i + 0.5f) * inv_d);
-    q -= (q * d > i);
-    q += ((q + 1) * d <= i);
-    return q;
+    return Divisor{((1ull << 40) + (uint64_t)d - 1) / (uint64_t)d, d};
+}
+__device__ __forceinline__ int fast_div(int i, const Divisor& v)
+{
+    return (int)(((uint64_t)(unsigned)i * v.m) >> 40);
 }
 
 enum { kLoadElem = 0, kLoadPairs = 1, kLoadStaged = 2 };
+
+// Free columns before every ring row: the 4-wide reads of the vector path
+// may start up to 4 columns left of a row without leaving the slot.
+constexpr int kRingMargin = 4;
 
 template <class T, int DIM, int SHAPE, int R, int NT, int ILP, int PF, int STG, int MINB>
 __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TBParams prm)
@@ -79,6 +90,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
     // coefficients in registers when they are few, else broadcast from shared memory
     constexpr bool kCoefRegs = (P * sizeof(typename DT<T>::C) <= (MINB >= 4 ? 40 : 128));
     constexpr auto OFF = St::kOff;
+    constexpr auto ROWS = St::make_rows();
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const ring = reinterpret_cast<T*>(smem_raw);
@@ -201,13 +213,16 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
         const int lo01 = (int)lo_s(a1, RP1, 0, pad1), hi01 = (int)hi_s(b1, n1, RP1, 0, pad1);
         const int lo02 = (int)lo_s(a2, R, 0, pad), hi02 = (int)hi_s(b2, n2, R, 0, pad);
         const int E1 = hi01 - lo01, E2 = hi02 - lo02;
-        const int E2p = (E2 + 3) & ~1;  // ring row pitch: even, room for the pair-load shift
+        // ring row: kRingMargin free columns, the row (+1 for the pair-load
+        // shift), then room for the 4-wide reads of the vector path (up to
+        // 7 columns past the row's last quad start); multiple of 4
+        const int E2p = (E2 + kRingMargin + 7 + 3) & ~3;
         const int plane0 = E1 * E2;
         if (E1 * E2p > plane_cap || (mode == kLoadStaged && plane0 > STG * NT)) {
             if (tid == 0) atomicCAS(&ctl->status, 0, 7 /* EBISU_ERR_DEVICE_FAULT */);
             return;
         }
-        const float invE2 = 1.0f / (float)E2;
+        const Divisor divE2 = make_divisor(E2);
         const int safe_off = (E1 / 2) * E2p + E2 / 2;  // >= R away from every plane edge
 
         // stored element offset of (ps, q1, q2), interior coordinates
@@ -225,8 +240,8 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
         // ring slot of plane ps at level lev (0 = input ring)
         auto ring_plane = [&](int lev, int64_t ps) -> T* {
             const unsigned rel = (unsigned)(ps - slo0);
-            if (lev == 0) return ring + (size_t)(rel % Q0) * plane_cap;
-            return ring + ((size_t)Q0 + (size_t)(lev - 1) * Q + (rel % Q)) * plane_cap;
+            if (lev == 0) return ring + (size_t)(rel % Q0) * plane_cap + kRingMargin;
+            return ring + ((size_t)Q0 + (size_t)(lev - 1) * Q + (rel % Q)) * plane_cap + kRingMargin;
         };
         // shift of a level-0 plane in pair-load mode: parity of its first
         // stored element (every row of a plane shares it, see host checks)
@@ -275,7 +290,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             const int64_t pb = gplane(ps);
             if (mode == kLoadElem) {
                 for (int i = tid; i < plane0; i += NT) {
-                    const int r1 = (DIM == 3) ? fast_div(i, invE2, E2) : 0;
+                    const int r1 = (DIM == 3) ? fast_div(i, divE2) : 0;
                     const int c2 = i - r1 * E2;
                     cp_async(rp + r1 * E2p + c2, src + pb + ginplane(lo01 + r1, lo02 + c2), (int)sizeof(T));
                 }
@@ -299,7 +314,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
                 for (int k = 0; k < kStg; ++k) {
                     const int i = tid + k * NT;
                     if (i < plane0) {
-                        const int r1 = (DIM == 3) ? fast_div(i, invE2, E2) : 0;
+                        const int r1 = (DIM == 3) ? fast_div(i, divE2) : 0;
                         const int c2 = i - r1 * E2;
                         stage[k] = D::raw(src + pb + ginplane(lo01 + r1, lo02 + c2));
                     }
@@ -312,7 +327,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             for (int k = 0; k < kStg; ++k) {
                 const int i = tid + k * NT;
                 if (i < plane0) {
-                    const int r1 = (DIM == 3) ? fast_div(i, invE2, E2) : 0;
+                    const int r1 = (DIM == 3) ? fast_div(i, divE2) : 0;
                     rp[r1 * E2p + (i - r1 * E2)] = stage[k];
                 }
             }
@@ -324,7 +339,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             const int l2 = (int)lo_s(a2, R, s, pad), h2 = (int)hi_s(b2, n2, R, s, pad);
             const int R2 = h2 - l2;
             const int cnt = (h1 - l1) * R2;
-            const float invR2 = 1.0f / (float)R2;
+            const Divisor divR2 = make_divisor(R2);
             const bool to_global = (s == d);
             T* const outp = to_global ? nullptr : ring_plane(s, ps);
             T* const gout = to_global ? dst + gplane(ps) : nullptr;
@@ -335,7 +350,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             const bool edge = !per && (pad_plane || l1 < 0 || h1 > n1 || l2 < 0 || h2 > n2);
             if (pad_plane) {  // keep the input values: copy from the level below
                 for (int i = tid; i < cnt; i += NT) {
-                    const int r1 = (DIM == 3) ? fast_div(i, invR2, R2) : 0;
+                    const int r1 = (DIM == 3) ? fast_div(i, divR2) : 0;
                     const int off = (l1 + r1 - lo01) * E2p + (l2 + (i - r1 * R2) - lo02);
                     outp[off] = self[off];
                 }
@@ -349,7 +364,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             }
             // cell index i -> (q1, q2) of this level's region
             auto cell = [&](int i, int& q1, int& q2) {
-                const int r1 = (DIM == 3) ? fast_div(i, invR2, R2) : 0;
+                const int r1 = (DIM == 3) ? fast_div(i, divR2) : 0;
                 q1 = l1 + r1;
                 q2 = l2 + (i - r1 * R2);
             };
@@ -415,6 +430,94 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             }
         };
 
+
+        // ---- FP32 storage: four consecutive cells per thread ------------------
+        // Each thread owns ring columns [4j, 4j+4) of a row and reads its
+        // neighbourhood as aligned 4-wide shared loads (one per needed quad of
+        // each stencil row), selecting neighbours from registers; the FMA
+        // chain of every cell is the canonical one, so results are identical
+        // to the scalar path and to the naive kernel.
+        auto compute_plane_vec = [&](int s, int64_t ps) {
+            const int l1 = (int)lo_s(a1, RP1, s, pad1), h1 = (int)hi_s(b1, n1, RP1, s, pad1);
+            const int l2 = (int)lo_s(a2, R, s, pad), h2 = (int)hi_s(b2, n2, R, s, pad);
+            const int c0 = l2 - lo02, c1 = h2 - lo02;  // ring columns of the region
+            const int jq0 = c0 >> 2, nq = ((c1 - 1) >> 2) - jq0 + 1;
+            const int items = (h1 - l1) * nq;
+            const Divisor divnq = make_divisor(nq);
+            const bool to_global = (s == d);
+            T* const outp = to_global ? nullptr : ring_plane(s, ps);
+            T* const gout = to_global ? dst + gplane(ps) : nullptr;
+            const T* const self = ring_plane(s - 1, ps);
+            const bool pad_plane = !per && (ps < 0 || ps >= n0);
+            const bool edge = !per && (pad_plane || l1 < 0 || h1 > n1 || l2 < 0 || h2 > n2);
+            const T* base[2 * R + 1];
+#pragma unroll
+            for (int k = 0; k < 2 * R + 1; ++k) base[k] = ring_plane(s - 1, ps + k - R);
+            for (int it = tid; it < items; it += NT) {
+                const int r1 = (DIM == 3) ? fast_div(it, divnq) : 0;
+                const int cb = 4 * (jq0 + it - r1 * nq);  // ring column of the first cell
+                const int q1 = l1 + r1;
+                const int rowoff = (q1 - lo01) * E2p;
+                C acc[4];
+                // a pad row of a 3D plane keeps its input values; its
+                // neighbour rows may lie outside the ring, so read nothing
+                const bool pad_row = !per && DIM == 3 && (q1 < 0 || q1 >= n1);
+                if (!pad_plane && !pad_row) {
+                    float w[12];
+#pragma unroll
+                    for (int k = 0; k < P; ++k) {
+                        if (ROWS.start[k]) {
+                            const T* rp = base[OFF.ds[k] + R] + rowoff + OFF.d1[k] * E2p + cb;
+                            const float4 mid = *reinterpret_cast<const float4*>(rp);
+                            w[4] = mid.x; w[5] = mid.y; w[6] = mid.z; w[7] = mid.w;
+                            if (ROWS.min_d2[k] < 0) {
+                                const float4 lft = *reinterpret_cast<const float4*>(rp - 4);
+                                w[0] = lft.x; w[1] = lft.y; w[2] = lft.z; w[3] = lft.w;
+                            }
+                            if (ROWS.max_d2[k] > 0) {
+                                const float4 rgt = *reinterpret_cast<const float4*>(rp + 4);
+                                w[8] = rgt.x; w[9] = rgt.y; w[10] = rgt.z; w[11] = rgt.w;
+                            }
+                        }
+                        const C ck = kCoefRegs ? cr[k] : s_coef[k];
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const C v = w[4 + m + OFF.d2[k]];
+                            acc[m] = (k == 0) ? D::mul(ck, v) : D::fma(ck, v, acc[m]);
+                        }
+                    }
+                }
+                // results: cells outside the region are skipped, pad cells keep
+                // the level below's value
+                T res[4];
+                bool keep[4], padc[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int col = cb + m;
+                    const int q2 = lo02 + col;
+                    keep[m] = (col >= c0) && (col < c1);
+                    padc[m] = edge && (pad_plane || q1 < 0 || q1 >= n1 || q2 < 0 || q2 >= n2);
+                    res[m] = padc[m] ? self[rowoff + col] : D::narrow(acc[m]);
+                }
+                if (to_global) {
+                    // per-cell addresses: on periodic grids a quad may straddle
+                    // the wrap, so its cells are not one contiguous run
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        if (keep[m] && !padc[m]) gout[ginplane(q1, lo02 + cb + m)] = res[m];
+                } else {
+                    T* op = outp + rowoff + cb;
+                    if (keep[0] && keep[3]) {
+                        *reinterpret_cast<float4*>(op) = make_float4(res[0], res[1], res[2], res[3]);
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            if (keep[m]) op[m] = res[m];
+                    }
+                }
+            }
+        };
+
         // ---- stream the tile ----------------------------------------------------
         auto lag = [&](int s) -> int64_t { return (int64_t)R + (int64_t)(s - 1) * (R + 1); };
         const int64_t lastp = bs - 1;  // last plane of level d
@@ -443,7 +546,12 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             }
             for (int s = 1; s <= d; ++s) {
                 const int64_t ps = slo0 + j - lag(s);
-                if (ps >= lo_s(as, R, s, pad) && ps < hi_s(bs, n0, R, s, pad)) compute_plane(s, ps);
+                if (ps >= lo_s(as, R, s, pad) && ps < hi_s(bs, n0, R, s, pad)) {
+                    if constexpr (std::is_same<T, float>::value)
+                        compute_plane_vec(s, ps);
+                    else
+                        compute_plane(s, ps);
+                }
             }
             if (mode == kLoadStaged && have_next) finish_staged(pnext);
         }

@@ -99,6 +99,7 @@ SIGNATURES = {
     "ebisu_serve_wait": (_I, [_P, ctypes.c_uint64, _D, ctypes.POINTER(_D)]),
     "ebisu_serve_stats": (_I, [_P, ctypes.POINTER(_I64)]),
     "ebisu_serve_cancel": (_I, [_P, ctypes.c_uint64]),
+    "ebisu_serve_set_max_queue": (_I, [_P, _I]),
     "ebisu_serve_destroy": (_I, [_P]),
     "ebisu_probe_device": (_I, [ctypes.POINTER(_D)]),
 }
@@ -386,6 +387,9 @@ class Server:
         _check(lib().ebisu_serve_wait(self.h, ctypes.c_uint64(ticket), float(timeout_s), ctypes.byref(lat)),
                "ebisu_serve_wait")
         return lat.value
+
+    def set_max_queue(self, n: int):
+        _check(lib().ebisu_serve_set_max_queue(self.h, int(n)), "ebisu_serve_set_max_queue")
 
     def cancel(self, ticket) -> int:
         return int(lib().ebisu_serve_cancel(self.h, ctypes.c_uint64(ticket)))

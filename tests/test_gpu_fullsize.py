@@ -1,0 +1,114 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark times.
+
+* 2D FP64 set on 8192 x 8192, 1000 steps: the parameters are chosen exactly
+  as bench.py chooses them (cost-model ranking + short timed tuning), then the
+  whole run is checked on sampled outputs the oracle can compute: corner
+  windows whose dependency cone (r cells per step) is cut out of the grid and
+  stepped by the oracle.  Cells farther than r*T from the cut's artificial
+  edge are exact functions of the cut, so the comparison is exact up to
+  rounding (relative L-inf 1e-12).
+* 3D FP64 set on 512^3, 200 steps: Dirichlet corner windows for the radius-1
+  stencils, and for every stencil a periodic run started from a cosine mode,
+  checked against the closed form lambda(k)^T (Fourier-mode decay).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_07390_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+TOL = 1e-12
+
+
+def _eb():
+    from paper_2305_07390_gb300 import ebisu
+    return ebisu
+
+
+def tuned_run(eb, ndim, dims, shape, r, c, g, steps, boundary=0, tune=8):
+    plan = eb.Plan(ndim, dims, shape, r, c, eb.F64, boundary)
+    x = torch.from_numpy(g).cuda()
+    y = torch.empty_like(x)
+    ws = plan.workspace()
+    plan.tune(x, y, min(steps, 16), ws, max_candidates=tune)  # as bench.py does
+    plan.run(x, y, steps, ws)
+    assert plan.sync(ws) == 0
+    return plan, y
+
+
+def corner_check(g, out, shape, r, c, steps, w, high):
+    """Oracle on the cone of a w^d corner window; returns rel L-inf error."""
+    nd = g.ndim
+    span = w + 2 * r + steps * r
+    if high:
+        sl = tuple(slice(s - span, s) for s in g.shape)
+    else:
+        sl = tuple(slice(0, span) for _ in g.shape)
+    cut = np.ascontiguousarray(g[sl])
+    ref = oracle.run(cut, shape, r, c, synth.DIRICHLET, steps)
+    if high:
+        win = tuple(slice(span - r - w, span - r) for _ in range(nd))
+    else:
+        win = tuple(slice(r, r + w) for _ in range(nd))
+    dev = out[sl][win]
+    ref_w = ref[win]
+    return float(np.max(np.abs(dev - ref_w)) / np.max(np.abs(ref_w)))
+
+
+@pytest.mark.parametrize("shape,r", [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2)])
+def test_2d_fullsize_corners(shape, r):
+    eb = _eb()
+    dims = (8192, 8192)
+    steps = 1000
+    g, c = synth.problem(2, dims, shape, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED + 17 * r + shape)
+    plan, y = tuned_run(eb, 2, dims, shape, r, c, g, steps)
+    out = y.cpu().numpy()
+    w = 6
+    assert corner_check(g, out, shape, r, c, steps, w, high=False) <= TOL
+    if r == 1:
+        assert corner_check(g, out, shape, r, c, steps, w, high=True) <= TOL
+    # the pad is untouched
+    assert np.array_equal(out[:r], g[:r]) and np.array_equal(out[:, -r:], g[:, -r:])
+
+
+@pytest.mark.parametrize("shape,r", [(0, 1), (1, 1)])
+def test_3d_fullsize_dirichlet_corners(shape, r):
+    eb = _eb()
+    dims = (512, 512, 512)
+    steps = 200
+    g, c = synth.problem(3, dims, shape, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED + 31 * r + shape)
+    plan, y = tuned_run(eb, 3, dims, shape, r, c, g, steps, tune=4)
+    out = y.cpu().numpy()
+    assert corner_check(g, out, shape, r, c, steps, 4, high=False) <= TOL
+    assert corner_check(g, out, shape, r, c, steps, 4, high=True) <= TOL
+
+
+@pytest.mark.parametrize("shape,r", [(0, 1), (0, 2), (1, 1), (1, 2)])
+@pytest.mark.parametrize("k", [(1, 1, 1), (2, 1, 3)])
+def test_3d_fullsize_periodic_fourier(shape, r, k):
+    eb = _eb()
+    dims = (512, 512, 512)
+    steps = 200
+    c = synth.coefficients(3, shape, r, dims, synth.PERIODIC, seed=synth.DEFAULT_SEED + 7)
+    u0 = synth.cosine_mode(dims, k)
+    plan, y = tuned_run(eb, 3, dims, shape, r, c, u0, steps, boundary=eb.PERIODIC, tune=3)
+    offs = oracle.offsets(3, shape, r)
+    lam = sum(ck * np.exp(2j * math.pi * sum(kd * od / nd for kd, od, nd in zip(k, o, dims)))
+              for o, ck in zip(offs, c))
+    assert abs(lam) ** steps > 1e-3
+    # compare on the device in slabs (the 512^3 reference is 1 GB)
+    lamT = lam ** steps
+    err = 0.0
+    xs = torch.arange(512, dtype=torch.float64, device="cuda")
+    for z0 in range(0, 512, 64):
+        zz, yy, xx = torch.meshgrid(xs[z0:z0 + 64], xs, xs, indexing="ij")
+        ph = 2 * math.pi * (k[0] * zz / 512 + k[1] * yy / 512 + k[2] * xx / 512)
+        ref = lamT.real * torch.cos(ph) - lamT.imag * torch.sin(ph)
+        err = max(err, float(torch.max(torch.abs(y[z0:z0 + 64] - ref))))
+    assert err / abs(lamT) <= TOL  # relative L-inf against the mode's amplitude
