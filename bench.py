@@ -133,6 +133,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_replicas(local_ms, local_updates, dist=None, device="cuda"):
+    """Replicas (weak scaling): every rank solves its own copy of the work.
+    Returns (max time over ranks in ms, total updates over ranks, world size);
+    the job's throughput is total updates / max time."""
+    if dist is None or not dist.is_initialized():
+        return float(local_ms), float(local_updates), 1
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item()), dist.get_world_size()
+
+
 def run_case(args):
     """One solve of one stencil (for ncu captures of a single kernel)."""
     import torch
@@ -154,6 +168,60 @@ def run_case(args):
     assert rc == 0, ebisu.status_string(rc)
     print(json.dumps({"case": args.case, "n": args.n, "dtype": args.dtype, "steps": args.solve_steps,
                       "params": plan.params().as_dict(), "naive": args.naive}))
+
+
+def run_set3d(args):
+    """3D FP64 stencil set on 512^3, 200 steps each (Dirichlet, pad = radius):
+    7- and 13-point stars, 27- and 125-point boxes, plus the 7-point star on a
+    periodic grid; fused kernel (parameters from the autotuner) against the
+    one-step-per-launch kernel on the same grids."""
+    import torch
+    from paper_2305_07390_gb300 import ebisu, synth
+    n, steps = 512, 200
+    stream = torch.cuda.current_stream()
+    sh = ebisu.current_stream_handle()
+    rows = []
+    for name, shape, r, bd in (("star r1", 0, 1, 0), ("star r2", 0, 2, 0), ("box r1", 1, 1, 0),
+                               ("box r2", 1, 2, 0), ("star r1 periodic", 0, 1, 1)):
+        dims = (n, n, n)
+        g, c = synth.problem(3, dims, shape, r, bd, seed=synth.DEFAULT_SEED + 31 * r + shape)
+        plan = ebisu.Plan(3, dims, shape, r, c, ebisu.F64, bd)
+        x = torch.from_numpy(g).cuda()
+        y = torch.empty_like(x)
+        ws = plan.workspace()
+        del g
+        plan.tune(x, y, 8, ws, max_candidates=args.tune)
+        pref = plan.params().variant
+        plan.set_params(variant=0)
+        plan.run(x, y, steps, ws, stream=sh)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.run(x, y, steps, ws, stream=sh)
+        b.record(stream)
+        b.synchronize()
+        assert plan.sync(ws) == 0
+        ms = a.elapsed_time(b)
+        ns = 20
+        a.record(stream)
+        plan.run(x, y, ns, ws, stream=sh, naive=True)
+        b.record(stream)
+        b.synchronize()
+        ms_naive = a.elapsed_time(b)
+        P = npoints3(shape, r)
+        rate = n ** 3 * steps / (ms * 1e-3)
+        rows.append({"stencil": name, "points": P, "ms": ms, "cell_updates_per_s": rate,
+                     "roofline_frac": rate * 2 * P / FP64_PEAK_FLOPS,
+                     "naive_cell_updates_per_s": n ** 3 * ns / (ms_naive * 1e-3),
+                     "tuner_preferred": "naive" if pref == 1 else "fused",
+                     "params": plan.params().as_dict()})
+        print(json.dumps(rows[-1]), flush=True)
+        del x, y, ws, plan
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": f"3D FP64 stencil set, {n}^3, {steps} steps", "rows": rows}), flush=True)
+
+
+def npoints3(shape, r):
+    return 6 * r + 1 if shape == 0 else (2 * r + 1) ** 3
 
 
 def run_batch(args):
@@ -312,7 +380,7 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="--case: storage type")
     ap.add_argument("--params", default="", help="--case: plan parameters, k=v,k=v")
     ap.add_argument("--naive", action="store_true", help="--case: the one-step-per-launch kernel")
-    ap.add_argument("--workload", default="set", choices=["set", "batch", "serve"],
+    ap.add_argument("--workload", default="set", choices=["set", "set3d", "batch", "serve"],
                     help="set: the FP64 2D stencil set (default, the headline line); batch: 512 uneven "
                          "2D 9-point box grids in one persistent launch per dtype; serve: Poisson arrivals "
                          "through the serving loop")
@@ -323,6 +391,8 @@ def main():
         return run_case(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "set3d":
+        return run_set3d(args)
     if args.workload == "serve":
         return run_serve(args)
     if args.warmup < 3:
@@ -365,6 +435,8 @@ def main():
     # timed run of the best few on this grid picks one (outside the timed region)
     for p in probs:
         p["plan"].tune(p["x"], p["y"], min(steps, 16), p["ws"], max_candidates=args.tune)
+        p["tuned_variant"] = p["plan"].params().variant
+        p["plan"].set_params(variant=0)  # the headline times the fused kernel
 
     def solve_all(events=None):
         for i, p in enumerate(probs):
@@ -403,12 +475,9 @@ def main():
     for p in probs:
         rc = p["plan"].sync(p["ws"])
         assert rc == 0, ebisu.status_string(rc)
-    if dist is not None:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
     upd_per_step = len(probs) * cells * steps
-    value = upd_per_step * args.steps * ws_n / (total_ms * 1e-3)
+    total_ms, total_upd, _ = aggregate_replicas(total_ms, upd_per_step * args.steps, dist)
+    value = total_upd / (total_ms * 1e-3)
 
     # per-stencil rates and the roofline of the dominant kernel (largest time)
     per = []
@@ -419,6 +488,18 @@ def main():
         per.append(dict(stencil=p["name"], points=p["P"], ms_per_launch=ms, cell_updates_per_s=rate,
                         tflops=flops / (ms * 1e-3) / 1e12, roofline_frac=flops / (ms * 1e-3) / FP64_PEAK_FLOPS,
                         params=p["plan"].params().as_dict()))
+    # the one-step-per-launch kernel on the same grid (100 steps, scaled)
+    for p, d in zip(probs, per):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nsteps = min(steps, 100)
+        p["plan"].run(p["x"], p["y"], nsteps, p["ws"], stream=sh, naive=True)
+        a.record(stream)
+        p["plan"].run(p["x"], p["y"], nsteps, p["ws"], stream=sh, naive=True)
+        b.record(stream)
+        b.synchronize()
+        d["naive_cell_updates_per_s"] = cells * nsteps / (a.elapsed_time(b) * 1e-3)
+        d["speedup_vs_naive"] = d["cell_updates_per_s"] / d["naive_cell_updates_per_s"]
+        d["tuner_preferred"] = "naive" if p["tuned_variant"] == 1 else "fused"
     dom = max(per, key=lambda d: d["ms_per_launch"])
     achieved = dom["tflops"]
 

@@ -79,7 +79,9 @@ enum ebisu_boundary { EBISU_DIRICHLET = 0, EBISU_PERIODIC = 1 };
  *                    Section 6.1, is one 256-thread CTA per SM).
  *   threads        : threads per CTA (multiple of 32, <= 1024).
  *   variant        : 0 = temporally blocked persistent kernel, 1 = naive
- *                    one-step-per-launch kernel. */
+ *                    one-step-per-launch kernel (ebisu_run then takes the
+ *                    naive path; batches and the server always use the
+ *                    fused kernel with the tile and depth fields). */
 typedef struct ebisu_params {
     int32_t tile_x;
     int32_t tile_y;
@@ -194,10 +196,11 @@ const char* ebisu_last_cuda_error(void);
 
 /* Empirical autotuning (Sections 6.3-6.4: the cost model prunes, the
  * measurement decides).  Times up to `max_candidates` parameter sets from the
- * cost model's ranking on the caller's buffers (in is not modified; out and
- * workspace are overwritten) for `steps` steps each, keeps the fastest in
- * the plan and, if `best_ms` is not NULL, stores its time there.
- * Synchronises the stream. */
+ * cost model's ranking, plus the naive one-step kernel, on the caller's
+ * buffers (in is not modified; out and workspace are overwritten) for `steps`
+ * steps each.  The plan keeps the fastest fused-kernel parameters, with
+ * `variant` = 1 if the naive kernel was faster still; `best_ms` (optional)
+ * receives the fastest time.  Synchronises the stream. */
 int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out,
                     int64_t steps, void* workspace, int max_candidates,
                     double* best_ms, void* stream);

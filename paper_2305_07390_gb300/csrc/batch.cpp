@@ -82,8 +82,10 @@ int layout(ebisu_batch_s* b)
     const int n = b->n;
     std::map<Key, int> gid;
     for (int i = 0; i < n; ++i) {
+        // batches always run the fused kernel with the plan's tile and depth
+        // (a plan whose tuner preferred the one-step kernel keeps them too)
+        b->plans[i].prm.variant = 0;
         const ebisu_plan_s* p = &b->plans[i];
-        if (p->prm.variant != 0) return EBISU_ERR_UNSUPPORTED;
         if (b->steps[i] <= 0) continue;  // zero steps: plain copy, no kernel
         Key k{p->ndim, p->shape, p->radius, p->dtype, kernel_variant(p->dtype, p->prm.ctas_per_sm)};
         auto it = gid.find(k);

@@ -157,17 +157,27 @@ constexpr int kTBStage = 16;
 constexpr int kTBILP = 4;
 
 // Two builds of the blocked kernel per stencil:
-//   variant 0: up to 128 registers (2 resident CTAs), deep prefetch
-//              (4 planes in 2D, 2 in 3D);
+//   variant 0: up to 128 registers (2 resident CTAs), 3 planes of prefetch
+//              in 2D and 2 in 3D (so that 2048-cell planes fit twice per SM);
 //   variant 1 (FP64 only): up to 64 registers and 2 planes of prefetch, so
 //              that 4 CTAs fit on an SM.  The FP64 pipe only stays busy when
 //              enough warps are resident to cover the per-plane barrier.
 // tb_variant_prefetch() must agree with prefetch_planes() on the host.
 template <class T, int DIM, int SHAPE, int R, int V>
 struct TBInst {
-    static constexpr int PF = (V == 1) ? 2 : (DIM == 3 ? 2 : 4);
+    static constexpr int PF = (V == 1 || DIM == 3) ? 2 : 3;
     static constexpr int MINB = (V == 1) ? 4 : 2;
-    static const void* ptr() { return (const void*)&tb_kernel<T, DIM, SHAPE, R, kTBThreads, kTBILP, PF, kTBStage, MINB>; }
+    // 4-wide compute for the FP32-arithmetic types (FP32, BF16 storage);
+    // measured slower than the scalar path for FP64, whose FP64 pipe, not the
+    // shared-memory issue, is the bound
+    static constexpr int VEC = sizeof(T) == 8 ? 0 : 1;
+    // independent FMA chains per thread: the FP64 pipe's dependent-issue
+    // latency needs more of them than FP32 (128-register build only)
+    static constexpr int ILP = (sizeof(T) == 8 && V == 0) ? 8 : kTBILP;
+    static const void* ptr()
+    {
+        return (const void*)&tb_kernel<T, DIM, SHAPE, R, kTBThreads, ILP, PF, kTBStage, MINB, VEC>;
+    }
 };
 
 template <class T>

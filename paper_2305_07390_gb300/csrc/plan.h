@@ -32,7 +32,7 @@ constexpr int kStagePerThread = 16; // register-staged plane elements per thread
 // FP64 with 3 or more CTAs per SM uses the 64-register, 2-plane-prefetch build.
 inline int kernel_variant(int dtype, int ctas_per_sm) { return (dtype == EBISU_F64 && ctas_per_sm >= 3) ? 1 : 0; }
 // Input planes in flight (cp.async) of a build.
-inline int prefetch_planes(int ndim, int variant) { return (variant == 1 || ndim == 3) ? 2 : 4; }
+inline int prefetch_planes(int ndim, int variant) { return (variant == 1 || ndim == 3) ? 2 : 3; }
 
 struct DeviceInfo {
     int device = -1;

@@ -73,11 +73,48 @@ __device__ __forceinline__ int fast_div(int i, const Divisor& v)
 
 enum { kLoadElem = 0, kLoadPairs = 1, kLoadStaged = 2 };
 
+// Four consecutive ring values (16-byte aligned for float, 32-byte for double).
+__device__ __forceinline__ void load_quad(const float* p, float* w)
+{
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+__device__ __forceinline__ void load_quad(const double* p, double* w)
+{
+    const double2 a = *reinterpret_cast<const double2*>(p);
+    const double2 b = *reinterpret_cast<const double2*>(p + 2);
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+}
+// BF16: four values in one 8-byte shared load / store (8-byte aligned)
+__device__ __forceinline__ void load_quad(const __nv_bfloat16* p, float* w)
+{
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    w[0] = __uint_as_float(u.x << 16);
+    w[1] = __uint_as_float(u.x & 0xffff0000u);
+    w[2] = __uint_as_float(u.y << 16);
+    w[3] = __uint_as_float(u.y & 0xffff0000u);
+}
+__device__ __forceinline__ void store_quad(__nv_bfloat16* p, const __nv_bfloat16* v)
+{
+    const unsigned a = (unsigned)__bfloat16_as_ushort(v[0]) | ((unsigned)__bfloat16_as_ushort(v[1]) << 16);
+    const unsigned b = (unsigned)__bfloat16_as_ushort(v[2]) | ((unsigned)__bfloat16_as_ushort(v[3]) << 16);
+    *reinterpret_cast<uint2*>(p) = make_uint2(a, b);
+}
+__device__ __forceinline__ void store_quad(float* p, const float* v)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store_quad(double* p, const double* v)
+{
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
 // Free columns before every ring row: the 4-wide reads of the vector path
 // may start up to 4 columns left of a row without leaving the slot.
 constexpr int kRingMargin = 4;
 
-template <class T, int DIM, int SHAPE, int R, int NT, int ILP, int PF, int STG, int MINB>
+template <class T, int DIM, int SHAPE, int R, int NT, int ILP, int PF, int STG, int MINB, int VEC>
 __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TBParams prm)
 {
     using St = Stencil<DIM, SHAPE, R>;
@@ -91,6 +128,8 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
     constexpr bool kCoefRegs = (P * sizeof(typename DT<T>::C) <= (MINB >= 4 ? 40 : 128));
     constexpr auto OFF = St::kOff;
     constexpr auto ROWS = St::make_rows();
+    // 4-wide path (chosen per storage type by the build, see kernels_impl.cuh)
+    constexpr bool kVec = (VEC != 0);
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const ring = reinterpret_cast<T*>(smem_raw);
@@ -413,16 +452,18 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
                     }
                 }
             };
-            static_assert(ILP == 4, "slot dispatch below assumes ILP = 4");
+            static_assert(ILP == 4 || ILP == 8, "slot dispatch below handles ILP 4 and 8");
             for (int i0 = tid; i0 < cnt; i0 += ILP * NT) {
                 // slots that hold at least one cell of this warp (warp-uniform),
                 // so a short last pass issues no FMAs for empty slots
                 const int wbase = i0 - (tid & 31);
                 const int uw = min(ILP, (cnt - wbase + NT - 1) / NT);
-                if (uw >= 4)
-                    group(std::integral_constant<int, 4>{}, i0);
-                else if (uw == 3)
-                    group(std::integral_constant<int, 3>{}, i0);
+                if (uw >= ILP)
+                    group(std::integral_constant<int, ILP>{}, i0);
+                else if (ILP == 8 && uw > 4)
+                    group(std::integral_constant<int, (ILP == 8 ? 6 : 1)>{}, i0);
+                else if (uw >= 3)
+                    group(std::integral_constant<int, (ILP == 8 ? 4 : 3)>{}, i0);
                 else if (uw == 2)
                     group(std::integral_constant<int, 2>{}, i0);
                 else
@@ -431,7 +472,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
         };
 
 
-        // ---- FP32 storage: four consecutive cells per thread ------------------
+        // ---- four consecutive cells per thread (FP32 and BF16 storage) ---------
         // Each thread owns ring columns [4j, 4j+4) of a row and reads its
         // neighbourhood as aligned 4-wide shared loads (one per needed quad of
         // each stencil row), selecting neighbours from registers; the FMA
@@ -451,8 +492,13 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             const bool pad_plane = !per && (ps < 0 || ps >= n0);
             const bool edge = !per && (pad_plane || l1 < 0 || h1 > n1 || l2 < 0 || h2 > n2);
             const T* base[2 * R + 1];
+            int shk[2 * R + 1];  // pair-load shift of each input plane (level 1, 2-byte storage)
 #pragma unroll
-            for (int k = 0; k < 2 * R + 1; ++k) base[k] = ring_plane(s - 1, ps + k - R);
+            for (int k = 0; k < 2 * R + 1; ++k) {
+                base[k] = ring_plane(s - 1, ps + k - R);
+                shk[k] = (s == 1) ? pshift(ps + k - R) : 0;
+            }
+            const int sh_self = (s == 1) ? pshift(ps) : 0;
             for (int it = tid; it < items; it += NT) {
                 const int r1 = (DIM == 3) ? fast_div(it, divnq) : 0;
                 const int cb = 4 * (jq0 + it - r1 * nq);  // ring column of the first cell
@@ -463,26 +509,21 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
                 // neighbour rows may lie outside the ring, so read nothing
                 const bool pad_row = !per && DIM == 3 && (q1 < 0 || q1 >= n1);
                 if (!pad_plane && !pad_row) {
-                    float w[12];
+                    C w[12];
 #pragma unroll
                     for (int k = 0; k < P; ++k) {
+                        // a shifted plane (sh = 1) holds column c at c + 1
+                        const int sh = shk[OFF.ds[k] + R];
                         if (ROWS.start[k]) {
                             const T* rp = base[OFF.ds[k] + R] + rowoff + OFF.d1[k] * E2p + cb;
-                            const float4 mid = *reinterpret_cast<const float4*>(rp);
-                            w[4] = mid.x; w[5] = mid.y; w[6] = mid.z; w[7] = mid.w;
-                            if (ROWS.min_d2[k] < 0) {
-                                const float4 lft = *reinterpret_cast<const float4*>(rp - 4);
-                                w[0] = lft.x; w[1] = lft.y; w[2] = lft.z; w[3] = lft.w;
-                            }
-                            if (ROWS.max_d2[k] > 0) {
-                                const float4 rgt = *reinterpret_cast<const float4*>(rp + 4);
-                                w[8] = rgt.x; w[9] = rgt.y; w[10] = rgt.z; w[11] = rgt.w;
-                            }
+                            load_quad(rp, w + 4);
+                            if (ROWS.min_d2[k] < 0) load_quad(rp - 4, w);
+                            if (ROWS.max_d2[k] > 0 || sh) load_quad(rp + 4, w + 8);
                         }
                         const C ck = kCoefRegs ? cr[k] : s_coef[k];
 #pragma unroll
                         for (int m = 0; m < 4; ++m) {
-                            const C v = w[4 + m + OFF.d2[k]];
+                            const C v = sh ? w[5 + m + OFF.d2[k]] : w[4 + m + OFF.d2[k]];
                             acc[m] = (k == 0) ? D::mul(ck, v) : D::fma(ck, v, acc[m]);
                         }
                     }
@@ -497,7 +538,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
                     const int q2 = lo02 + col;
                     keep[m] = (col >= c0) && (col < c1);
                     padc[m] = edge && (pad_plane || q1 < 0 || q1 >= n1 || q2 < 0 || q2 >= n2);
-                    res[m] = padc[m] ? self[rowoff + col] : D::narrow(acc[m]);
+                    res[m] = padc[m] ? self[rowoff + col + sh_self] : D::narrow(acc[m]);
                 }
                 if (to_global) {
                     // per-cell addresses: on periodic grids a quad may straddle
@@ -508,7 +549,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
                 } else {
                     T* op = outp + rowoff + cb;
                     if (keep[0] && keep[3]) {
-                        *reinterpret_cast<float4*>(op) = make_float4(res[0], res[1], res[2], res[3]);
+                        store_quad(op, res);
                     } else {
 #pragma unroll
                         for (int m = 0; m < 4; ++m)
@@ -547,7 +588,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             for (int s = 1; s <= d; ++s) {
                 const int64_t ps = slo0 + j - lag(s);
                 if (ps >= lo_s(as, R, s, pad) && ps < hi_s(bs, n0, R, s, pad)) {
-                    if constexpr (std::is_same<T, float>::value)
+                    if constexpr (kVec)
                         compute_plane_vec(s, ps);
                     else
                         compute_plane(s, ps);

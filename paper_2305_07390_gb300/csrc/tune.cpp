@@ -268,14 +268,22 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
     if (in == out) return EBISU_ERR_INVALID_ARG;
     std::vector<ebisu_params> cand(max_candidates);
     std::vector<double> pred(max_candidates);
-    const int n = rank_candidates(plan, steps, cand.data(), pred.data(), max_candidates);
+    int n = rank_candidates(plan, steps, cand.data(), pred.data(), max_candidates);
     if (n < 1) return EBISU_ERR_UNSUPPORTED;
+    // The one-step-per-launch kernel is timed too: where the fused kernel
+    // cannot beat it (measured: 3D low-order FP64 stars), the plan runs it.
+    ebisu_params naive = cand[0];
+    naive.variant = 1;
+    cand.push_back(naive);
+    ++n;
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail_cuda(cudaGetLastError());
     const ebisu_params saved = plan->prm;
     double best = 1e300;
     ebisu_params bestp = saved;
+    ebisu_params best_blocked = cand[0];
+    double best_blocked_ms = 1e300;
     int rc = EBISU_OK;
     for (int i = 0; i < n; ++i) {
         plan->prm = cand[i];
@@ -293,10 +301,21 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
             best = ms;
             bestp = cand[i];
         }
+        if (cand[i].variant == 0 && ms < best_blocked_ms) {
+            best_blocked_ms = ms;
+            best_blocked = cand[i];
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    plan->prm = (rc == EBISU_OK) ? bestp : saved;
+    if (rc == EBISU_OK) {
+        // keep the best fused-kernel parameters (batches and the server use
+        // them) and record which kernel won in `variant`
+        plan->prm = best_blocked;
+        plan->prm.variant = bestp.variant;
+    } else {
+        plan->prm = saved;
+    }
     if (best_ms) *best_ms = best;
     return rc;
 }
