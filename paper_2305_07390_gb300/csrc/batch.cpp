@@ -136,7 +136,7 @@ int layout(ebisu_batch_s* b)
         for (int m : g.members) {
             const ebisu_plan_s* p = &b->plans[m];
             const int d = (int)std::min<int64_t>(p->prm.depth, b->steps[m]);
-            const size_t slots = (size_t)ring_q0(p->radius, p->ndim, g.variant) + (size_t)(d - 1) * ring_q(p->radius);
+            const size_t slots = (size_t)ring_q0(p->radius, p->ndim, g.variant, p->esize) + (size_t)(d - 1) * ring_q(p->radius);
             need = std::max(need, slots * (size_t)g.plane_cap * p->esize);
         }
         g.smem = need;

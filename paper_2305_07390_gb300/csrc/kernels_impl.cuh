@@ -157,15 +157,16 @@ constexpr int kTBStage = 16;
 constexpr int kTBILP = 4;
 
 // Two builds of the blocked kernel per stencil:
-//   variant 0: up to 128 registers (2 resident CTAs), 3 planes of prefetch
-//              in 2D and 2 in 3D (so that 2048-cell planes fit twice per SM);
+//   variant 0: up to 128 registers (2 resident CTAs); prefetch 2 planes in
+//              3D, 3 in 2D FP64 (2048-wide FP64 rows still fit twice per SM)
+//              and 4 in 2D FP32/BF16;
 //   variant 1 (FP64 only): up to 64 registers and 2 planes of prefetch, so
 //              that 4 CTAs fit on an SM.  The FP64 pipe only stays busy when
 //              enough warps are resident to cover the per-plane barrier.
 // tb_variant_prefetch() must agree with prefetch_planes() on the host.
 template <class T, int DIM, int SHAPE, int R, int V>
 struct TBInst {
-    static constexpr int PF = (V == 1 || DIM == 3) ? 2 : 3;
+    static constexpr int PF = (V == 1 || DIM == 3) ? 2 : (sizeof(T) == 8 ? 3 : 4);
     static constexpr int MINB = (V == 1) ? 4 : 2;
     // 4-wide compute for the FP32-arithmetic types (FP32, BF16 storage);
     // measured slower than the scalar path for FP64, whose FP64 pipe, not the

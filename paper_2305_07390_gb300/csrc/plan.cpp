@@ -64,7 +64,10 @@ int64_t wait_timeout_ns()
 }
 
 int ring_q(int radius) { return 2 * radius + 2; }
-int ring_q0(int radius, int ndim, int variant) { return 2 * radius + 1 + prefetch_planes(ndim, variant); }
+int ring_q0(int radius, int ndim, int variant, size_t esize)
+{
+    return 2 * radius + 1 + prefetch_planes(ndim, variant, esize);
+}
 
 // largest level-0 region of any tile: (E1, E2), unpadded
 static void max_plane(const ebisu_plan_s* p, const ebisu_params& q, int64_t* e1, int64_t* e2)
@@ -94,7 +97,7 @@ int64_t plane_capacity(const ebisu_plan_s* p, const ebisu_params& q)
 
 size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q)
 {
-    const size_t slots = (size_t)ring_q0(p->radius, p->ndim, kernel_variant(p->dtype, q.ctas_per_sm)) +
+    const size_t slots = (size_t)ring_q0(p->radius, p->ndim, kernel_variant(p->dtype, q.ctas_per_sm), p->esize) +
                          (size_t)(q.depth - 1) * ring_q(p->radius);
     return slots * (size_t)plane_capacity(p, q) * p->esize;
 }

@@ -32,7 +32,10 @@ constexpr int kStagePerThread = 16; // register-staged plane elements per thread
 // FP64 with 3 or more CTAs per SM uses the 64-register, 2-plane-prefetch build.
 inline int kernel_variant(int dtype, int ctas_per_sm) { return (dtype == EBISU_F64 && ctas_per_sm >= 3) ? 1 : 0; }
 // Input planes in flight (cp.async) of a build.
-inline int prefetch_planes(int ndim, int variant) { return (variant == 1 || ndim == 3) ? 2 : 3; }
+inline int prefetch_planes(int ndim, int variant, size_t esize)
+{
+    return (variant == 1 || ndim == 3) ? 2 : (esize == 8 ? 3 : 4);
+}
 
 struct DeviceInfo {
     int device = -1;
@@ -54,7 +57,7 @@ void set_cuda_error(cudaError_t e);
 int fail_cuda(cudaError_t e);
 
 int ring_q(int radius);   // slots of a level-1.. ring (2r+2)
-int ring_q0(int radius, int ndim, int variant);  // slots of the input ring (2r+1+prefetch)
+int ring_q0(int radius, int ndim, int variant, size_t esize);  // input ring slots (2r+1+prefetch)
 // Elements per ring plane and dynamic shared memory of a parameter set.
 int64_t plane_capacity(const ebisu_plan_s* p, const ebisu_params& q);
 size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q);

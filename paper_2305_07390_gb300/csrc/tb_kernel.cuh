@@ -100,6 +100,22 @@ __device__ __forceinline__ void store_quad(__nv_bfloat16* p, const __nv_bfloat16
     const unsigned b = (unsigned)__bfloat16_as_ushort(v[2]) | ((unsigned)__bfloat16_as_ushort(v[3]) << 16);
     *reinterpret_cast<uint2*>(p) = make_uint2(a, b);
 }
+// 16-byte (FP32) / 8-byte (BF16) global store of an aligned quad
+__device__ __forceinline__ void store_quad_global(float* p, const float* v)
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store_quad_global(double* p, const double* v)
+{
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void store_quad_global(__nv_bfloat16* p, const __nv_bfloat16* v)
+{
+    const unsigned a = (unsigned)__bfloat16_as_ushort(v[0]) | ((unsigned)__bfloat16_as_ushort(v[1]) << 16);
+    const unsigned b = (unsigned)__bfloat16_as_ushort(v[2]) | ((unsigned)__bfloat16_as_ushort(v[3]) << 16);
+    *reinterpret_cast<uint2*>(p) = make_uint2(a, b);
+}
 __device__ __forceinline__ void store_quad(float* p, const float* v)
 {
     *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
@@ -498,7 +514,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
                 base[k] = ring_plane(s - 1, ps + k - R);
                 shk[k] = (s == 1) ? pshift(ps + k - R) : 0;
             }
-            const int sh_self = (s == 1) ? pshift(ps) : 0;
+            const int sh_self = (sizeof(T) == 2 && s == 1) ? pshift(ps) : 0;
             for (int it = tid; it < items; it += NT) {
                 const int r1 = (DIM == 3) ? fast_div(it, divnq) : 0;
                 const int cb = 4 * (jq0 + it - r1 * nq);  // ring column of the first cell
@@ -513,7 +529,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
 #pragma unroll
                     for (int k = 0; k < P; ++k) {
                         // a shifted plane (sh = 1) holds column c at c + 1
-                        const int sh = shk[OFF.ds[k] + R];
+                        const int sh = (sizeof(T) == 2) ? shk[OFF.ds[k] + R] : 0;
                         if (ROWS.start[k]) {
                             const T* rp = base[OFF.ds[k] + R] + rowoff + OFF.d1[k] * E2p + cb;
                             load_quad(rp, w + 4);
@@ -528,8 +544,29 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
                         }
                     }
                 }
-                // results: cells outside the region are skipped, pad cells keep
-                // the level below's value
+                // Interior quad (the common case): all four cells inside the
+                // region, no pad cell, one contiguous run in global memory.
+                const bool inner = (cb >= c0) && (cb + 4 <= c1) && !edge &&
+                                   (!per || (lo02 + cb >= 0 && lo02 + cb + 4 <= n2 && q1 >= 0 && q1 < n1));
+                if (inner) {
+                    T res[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) res[m] = D::narrow(acc[m]);
+                    if (to_global) {
+                        T* gp = gout + ginplane(q1, lo02 + cb);
+                        if ((reinterpret_cast<uintptr_t>(gp) & (4 * sizeof(T) - 1)) == 0) {
+                            store_quad_global(gp, res);
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < 4; ++m) gp[m] = res[m];
+                        }
+                    } else {
+                        store_quad(outp + rowoff + cb, res);
+                    }
+                    continue;
+                }
+                // general quad: cells outside the region are skipped, pad cells
+                // keep the level below's value
                 T res[4];
                 bool keep[4], padc[4];
 #pragma unroll

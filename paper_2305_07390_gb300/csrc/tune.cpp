@@ -116,10 +116,24 @@ double model_pp(const ebisu_plan_s* p, const ebisu_params& q, int64_t steps, int
     double useful = 0, loaded = 0;
     double computed = trapezoid_cells(p, g, t, &useful, &loaded);
     const double vsm = useful / computed;
-    // Partial warps: each level-plane region is processed in warp-wide
-    // slots; on average half a warp of a region's last slot is empty.
-    const double region = (double)g.tile[1] * g.tile[2];
-    computed *= 1.0 + 16.0 / std::max(region, 32.0);
+    // Partial passes.  The barrier after every streamed plane makes each
+    // level cost as much as its busiest thread: for 2-byte and 4-byte storage
+    // (four cells per thread) a level of width w costs ceil(quads / threads)
+    // full passes; for FP64 (one cell per slot) about half a warp of the last
+    // slot is empty.
+    if (p->esize <= 4 && p->ndim == 2) {
+        double eff_cells = 0, real_cells = 0;
+        for (int s = 1; s <= t; ++s) {
+            const double w = (double)g.tile[2] + 2.0 * p->radius * (t - s);
+            const double quads = std::ceil((w + 3.0) / 4.0);
+            eff_cells += std::ceil(quads / kThreads) * 4.0 * kThreads;
+            real_cells += w;
+        }
+        computed *= eff_cells / real_cells;
+    } else {
+        const double region = (double)g.tile[1] * g.tile[2];
+        computed *= 1.0 + 16.0 / std::max(region, 32.0);
+    }
     const double S = (double)p->esize;
     const double cells = (double)g.n[0] * g.n[1] * g.n[2];
     const double thr = (p->dtype == EBISU_F64) ? dv.f64 : dv.f32;
@@ -176,7 +190,16 @@ int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, dou
     }
     for (int d : depths) {
         if (d > std::max<int64_t>(steps, 1) && d != 1) continue;
-        for (int tx : txs)
+        std::vector<int> txd = txs;
+        if (p->ndim == 2 && p->esize <= 4) {
+            // widths whose widest level (w + r(2d-1) + alignment) fills whole
+            // passes of four cells per thread
+            for (int k : {1, 2, 3}) {
+                const int w = (4 * kThreads * k - p->radius * (2 * d - 1) - 4) & ~3;
+                if (w >= 64) push_unique(txd, (int)std::min<int64_t>(w, p->n[2]));
+            }
+        }
+        for (int tx : txd)
             for (int ty : tys)
                 for (int cps : {1, 2, 4}) {
                     if (cps == 4 && p->dtype != EBISU_F64) continue;
