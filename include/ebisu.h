@@ -78,10 +78,17 @@ enum ebisu_boundary { EBISU_DIRICHLET = 0, EBISU_PERIODIC = 1 };
  *   ctas_per_sm    : resident CTAs per SM (the paper's minimal parallelism,
  *                    Section 6.1, is one 256-thread CTA per SM).
  *   threads        : threads per CTA (multiple of 32, <= 1024).
- *   variant        : 0 = temporally blocked persistent kernel, 1 = naive
- *                    one-step-per-launch kernel (ebisu_run then takes the
- *                    naive path; batches and the server always use the
- *                    fused kernel with the tile and depth fields). */
+ *   variant        : 0 = temporally blocked persistent kernel (shared-
+ *                    memory queues), 1 = naive one-step-per-launch kernel
+ *                    (ebisu_run then takes the naive path), 2 = register-
+ *                    streaming temporally blocked kernel (2D only): one warp
+ *                    per 128-column strip, every time level in registers;
+ *                    depth must be one of ebisu_plan_rs_depths(), tile_s is
+ *                    the rows per strip segment, ctas_per_sm caps the
+ *                    resident 128-thread CTAs, and tile_x is set to the
+ *                    strip's output width 128 - 2*depth*radius.  Batches and
+ *                    the server always run variant 0 with the last variant-0
+ *                    parameters the plan held. */
 typedef struct ebisu_params {
     int32_t tile_x;
     int32_t tile_y;
@@ -90,7 +97,11 @@ typedef struct ebisu_params {
     int32_t ctas_per_sm;
     int32_t threads;
     int32_t variant;
-    int32_t reserved;
+    int32_t fused_variant;  /* set by ebisu_plan_tune: the faster temporally
+                             * blocked build (0 or 2).  When the tuner picks
+                             * the naive kernel (variant 1), the tile and
+                             * depth fields are that build's parameters, so
+                             * setting variant = fused_variant runs it. */
 } ebisu_params;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -132,6 +143,12 @@ int ebisu_plan_grid_elems(ebisu_plan_t plan, int64_t* elems);
  * EBISU_ERR_UNSUPPORTED if they cannot run. */
 int ebisu_plan_get_params(ebisu_plan_t plan, ebisu_params* p);
 int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* p);
+
+/* Temporal depths built for the register-streaming kernel (variant 2) of
+ * this plan's stencil and storage type (Section 4's temporal blocking with
+ * the per-level queues held in registers): *shallow <= *deep.  Both are 0
+ * for 3D plans (no such kernel).  Host only; never fails for a valid plan. */
+int ebisu_plan_rs_depths(ebisu_plan_t plan, int* shallow, int* deep);
 
 /* Bytes of device workspace a run of this plan needs: a control block plus
  * one grid-sized ping-pong buffer (the paper's two time levels, Listing 4). */

@@ -84,6 +84,7 @@ int layout(ebisu_batch_s* b)
     for (int i = 0; i < n; ++i) {
         // batches always run the fused kernel with the plan's tile and depth
         // (a plan whose tuner preferred the one-step kernel keeps them too)
+        b->plans[i].prm = b->plans[i].tb_prm;
         b->plans[i].prm.variant = 0;
         const ebisu_plan_s* p = &b->plans[i];
         if (b->steps[i] <= 0) continue;  // zero steps: plain copy, no kernel

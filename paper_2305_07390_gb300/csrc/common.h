@@ -6,7 +6,7 @@
 namespace ebisu {
 
 constexpr int kMaxPoints = 125;        // 3D box of radius 2
-constexpr size_t kControlBytes = 4096; // status word, counters (single run)
+constexpr size_t kControlBytes = 65536; // status word, counters (single run)
 constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -58,6 +58,50 @@ struct TBParams {
     int32_t debug_stall;        // test hook: 1 = the first wait targets a
                                 // count that is never reached
     int32_t smem_plane;         // elements per ring plane
+};
+
+// ---------------------------------------------------------------------------
+// Register-streaming build (2D): one warp streams one strip of 128 columns
+// (32 lanes x 4 cells) down a segment of rows, every time level of the
+// temporal block held in registers.  Tiles of one temporal block depend only
+// on their eight neighbours of the previous block (per-tile counters).
+constexpr int kRSWarps = 4;            // warps per CTA
+constexpr int kRSThreads = 32 * kRSWarps;
+constexpr int kRSCols = 128;           // columns a warp holds (loaded region)
+// Maximum tiles of one run (one completion counter each in the Control block).
+constexpr int64_t kRSMaxTiles = (int64_t)((kControlBytes - 64) / sizeof(unsigned));
+
+// Temporal depths built per storage size and stencil (which = 0: the
+// shallower, 1: the deeper).  FP64 is bound by its FMA pipe, so depth only
+// adds redundant work there; FP32/BF16 take the deepest ring that still fits
+// the register file at two or more resident CTAs.
+constexpr int rs_depth(int esize, int shape /*0 star, 1 box*/, int r, int which)
+{
+    if (esize == 8) return (which && !(shape == 0 && r == 3) && !(shape == 1 && r == 2)) ? 2 : 1;
+    if (shape == 0) return r == 1 ? (which ? 8 : 4) : r == 2 ? (which ? 5 : 3) : (which ? 3 : 2);
+    return r == 1 ? (which ? 6 : 3) : (which ? 2 : 1);
+}
+
+struct RSParams {
+    const void* src0;   // input of the first temporal block
+    void* out;          // final destination
+    void* ws;           // ping-pong buffer
+    int64_t n0;         // interior rows
+    int64_t lds;        // row pitch (elements)
+    int64_t nitems;     // nblocks * nstrips * nsegs
+    Control* ctl;
+    int64_t timeout_ns;
+    int32_t n2;         // interior columns
+    int32_t pad;        // Dirichlet pad (= radius), 0 if periodic
+    int32_t periodic;
+    int32_t S;          // output columns per strip (128 - 2 * depth * radius)
+    int32_t H;          // output rows per segment
+    int32_t nstrips, nsegs;
+    int32_t nblocks;    // ceil(steps / depth)
+    int32_t depth_last; // steps done by the last block (<= depth)
+    int32_t debug_stall;
+    double coef[kMaxPoints];
+    float coef_f[kMaxPoints];  // the same rounded to FP32 (FP32/BF16 storage)
 };
 
 }  // namespace ebisu

@@ -14,6 +14,7 @@ struct NaiveParams {
     int32_t pad;
     int32_t periodic;
     double coef[kMaxPoints];
+    float coef_f[kMaxPoints];  // the same rounded to FP32 on the host (FP32/BF16 storage)
 };
 
 // Geometry of a stored grid for pad copies and reductions.
@@ -34,6 +35,14 @@ struct PadParams {
                                 cudaStream_t st);                                                \
     cudaError_t reduce_partial_##NAME(const void* a, const void* b, double* part,                \
                                       const PadParams& p, int64_t* n, cudaStream_t st);
+
+#define EBISU_DECLARE_RS_ENTRY(NAME)                                                               \
+    cudaError_t rs_launch_##NAME(int s, int r, int d, const RSParams& p, int g, cudaStream_t st);   \
+    cudaError_t rs_occupancy_##NAME(int s, int r, int d, int* b);
+
+EBISU_DECLARE_RS_ENTRY(f64)
+EBISU_DECLARE_RS_ENTRY(f32)
+EBISU_DECLARE_RS_ENTRY(bf16)
 
 EBISU_DECLARE_DTYPE_ENTRY(f64)
 EBISU_DECLARE_DTYPE_ENTRY(f32)

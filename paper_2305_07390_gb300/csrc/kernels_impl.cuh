@@ -32,6 +32,12 @@ __global__ void __launch_bounds__(256) naive_kernel(const T* __restrict__ src, T
     if (q2 >= n2 || q1 >= n1 || ps >= n0) return;
     const int pad = a.pad, pad1 = (DIM == 3) ? a.pad : 0;
     const int64_t lds = a.lds, ld1 = a.ld1;
+    // coefficients already in the accumulation type: a per-cell FP64 -> FP32
+    // conversion would run on the (slow) FP64 pipe
+    auto cf = [&](int k) -> C {
+        if constexpr (std::is_same<C, double>::value) return a.coef[k];
+        else return a.coef_f[k];
+    };
     C acc;
     if (a.periodic) {
         auto at = [&](int k) -> C {
@@ -40,17 +46,17 @@ __global__ void __launch_bounds__(256) naive_kernel(const T* __restrict__ src, T
             const int64_t x_ = wrap_idx(q2 + OFF.d2[k], n2);
             return D::load_ro(src + s_ * lds + y_ * ld1 + x_);
         };
-        acc = D::mul(D::coef(a.coef[0]), at(0));
+        acc = D::mul(cf(0), at(0));
 #pragma unroll
-        for (int k = 1; k < P; ++k) acc = D::fma(D::coef(a.coef[k]), at(k), acc);
+        for (int k = 1; k < P; ++k) acc = D::fma(cf(k), at(k), acc);
         dst[ps * lds + (int64_t)q1 * ld1 + q2] = D::narrow(acc);
     } else {
         const int64_t c = (ps + pad) * lds + (int64_t)(q1 + pad1) * ld1 + (q2 + pad);
         const T* p = src + c;
         auto at = [&](int k) -> C { return D::load_ro(p + OFF.ds[k] * lds + OFF.d1[k] * ld1 + OFF.d2[k]); };
-        acc = D::mul(D::coef(a.coef[0]), at(0));
+        acc = D::mul(cf(0), at(0));
 #pragma unroll
-        for (int k = 1; k < P; ++k) acc = D::fma(D::coef(a.coef[k]), at(k), acc);
+        for (int k = 1; k < P; ++k) acc = D::fma(cf(k), at(k), acc);
         dst[c] = D::narrow(acc);
     }
 }

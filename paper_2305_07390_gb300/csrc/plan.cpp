@@ -102,10 +102,43 @@ size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q)
     return slots * (size_t)plane_capacity(p, q) * p->esize;
 }
 
+int rs_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L)
+{
+    if (p->ndim != 2) return EBISU_ERR_UNSUPPORTED;
+    const int r = p->radius, es = (int)p->esize;
+    if (q.depth != rs_depth(es, p->shape, r, 0) && q.depth != rs_depth(es, p->shape, r, 1))
+        return EBISU_ERR_UNSUPPORTED;
+    const int64_t n0 = p->n[0], n2 = p->n[2];
+    if (n0 + 2 * p->pad > (1LL << 30) || n2 + 2 * p->pad > (1LL << 30)) return EBISU_ERR_UNSUPPORTED;
+    const bool per = p->boundary == EBISU_PERIODIC;
+    // the kernel wraps a periodic index at most once
+    if (per && (n0 < 64 || n2 < 136)) return EBISU_ERR_UNSUPPORTED;
+    const int dr = q.depth * r;
+    const int S = kRSCols - 2 * dr;
+    const int64_t H = (q.tile_s <= 0) ? n0 : std::min<int64_t>(q.tile_s, n0);
+    const int64_t ns = (n2 + S - 1) / S, ng = (n0 + H - 1) / H;
+    // a tile's inputs reach dr cells into its neighbours and no further
+    if (ng > 1 && H < dr) return EBISU_ERR_UNSUPPORTED;
+    if (per && ns > 1 && n2 - (ns - 1) * S < dr) return EBISU_ERR_UNSUPPORTED;
+    if (per && ng > 1 && n0 - (ng - 1) * H < dr) return EBISU_ERR_UNSUPPORTED;
+    if (ns * ng > kRSMaxTiles) return EBISU_ERR_UNSUPPORTED;
+    if (L) {
+        L->S = S;
+        L->H = (int)H;
+        L->nstrips = (int)ns;
+        L->nsegs = (int)ng;
+    }
+    return EBISU_OK;
+}
+
 int check_params(const ebisu_plan_s* p, const ebisu_params& q)
 {
-    if (q.variant != 0 && q.variant != 1) return EBISU_ERR_INVALID_ARG;
+    if (q.variant < 0 || q.variant > 2) return EBISU_ERR_INVALID_ARG;
     if (q.variant == 1) return EBISU_OK;
+    if (q.variant == 2) {
+        if (q.ctas_per_sm < 1 || q.ctas_per_sm > 16 || q.tile_s < 0) return EBISU_ERR_INVALID_ARG;
+        return rs_layout(p, q, nullptr);
+    }
     if (q.depth < 1 || q.depth > 64 || q.tile_x < 1 || (p->ndim == 3 && q.tile_y < 1) || q.tile_s < 0 ||
         q.ctas_per_sm < 1 || q.ctas_per_sm > 8)
         return EBISU_ERR_INVALID_ARG;
@@ -190,7 +223,10 @@ static NaiveParams naive_params(const ebisu_plan_s* p)
     a.ld1 = p->ld1;
     a.pad = p->pad;
     a.periodic = p->boundary == EBISU_PERIODIC;
-    for (int k = 0; k < p->npts; ++k) a.coef[k] = p->coef[k];
+    for (int k = 0; k < p->npts; ++k) {
+        a.coef[k] = p->coef[k];
+        a.coef_f[k] = (float)p->coef[k];  // round to nearest, as the device conversion does
+    }
     return a;
 }
 
@@ -231,6 +267,99 @@ cudaError_t pad_copy(const ebisu_plan_s* p, const void* src, void* d0, void* d1,
 
 // ===========================================================================
 // C ABI
+
+namespace ebisu {
+
+cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int grid, cudaStream_t st)
+{
+    switch (p->dtype) {
+    case EBISU_F64: return rs_launch_f64(p->shape, p->radius, depth, prm, grid, st);
+    case EBISU_F32: return rs_launch_f32(p->shape, p->radius, depth, prm, grid, st);
+    default: return rs_launch_bf16(p->shape, p->radius, depth, prm, grid, st);
+    }
+}
+
+cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, int* blocks)
+{
+    switch (p->dtype) {
+    case EBISU_F64: return rs_occupancy_f64(p->shape, p->radius, depth, blocks);
+    case EBISU_F32: return rs_occupancy_f32(p->shape, p->radius, depth, blocks);
+    default: return rs_occupancy_bf16(p->shape, p->radius, depth, blocks);
+    }
+}
+
+// A run of the register-streaming build (the control block is already zeroed
+// and steps >= 1).
+static int run_rs(ebisu_plan_t p, const void* in, void* out, int64_t steps, void* ws, cudaStream_t st,
+                  int debug_stall)
+{
+    const ebisu_params& q = p->prm;
+    RSLayout L;
+    int rc = rs_layout(p, q, &L);
+    if (rc != EBISU_OK) return rc;
+    const int D = q.depth;
+    const int64_t nb = (steps + D - 1) / D;
+    const int64_t ntiles = (int64_t)L.nstrips * L.nsegs;
+    const DeviceInfo& dv = device_info();
+    // the queue head is a 32-bit counter that every warp overshoots once
+    if (nb * ntiles + 64LL * 16 * dv.sms * kRSWarps >= (1LL << 32)) return EBISU_ERR_UNSUPPORTED;
+    const size_t bytes = (size_t)p->elems * p->esize;
+    void* wsgrid = (char*)ws + kControlBytes;
+    cudaError_t e = cudaSuccess;
+    const bool copy_in = (in == out) && (nb % 2 == 1);
+    if (copy_in) {
+        e = cudaMemcpyAsync(wsgrid, in, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return fail_cuda(e);
+    }
+    const void* src0 = copy_in ? wsgrid : in;
+    const bool per = p->boundary == EBISU_PERIODIC;
+    if (!per) {
+        // the kernel never writes pad cells: give the buffers it writes the input's pad
+        void* d0 = ((nb - 1) % 2 == 0) ? out : wsgrid;
+        void* d1 = (nb >= 2) ? (((nb - 2) % 2 == 0) ? out : wsgrid) : nullptr;
+        void* h0 = (d0 != src0 && d0 != in) ? d0 : nullptr;
+        void* h1 = (d1 && d1 != src0 && d1 != in) ? d1 : nullptr;
+        if (h0 || h1) {
+            e = pad_copy(p, src0, h0, h1, st);
+            if (e != cudaSuccess) return fail_cuda(e);
+        }
+    }
+    RSParams prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.src0 = src0;
+    prm.out = out;
+    prm.ws = wsgrid;
+    prm.n0 = p->n[0];
+    prm.lds = p->lds;
+    prm.nitems = nb * ntiles;
+    prm.ctl = (Control*)ws;
+    prm.timeout_ns = wait_timeout_ns();
+    prm.n2 = (int32_t)p->n[2];
+    prm.pad = p->pad;
+    prm.periodic = per ? 1 : 0;
+    prm.S = L.S;
+    prm.H = L.H;
+    prm.nstrips = L.nstrips;
+    prm.nsegs = L.nsegs;
+    prm.nblocks = (int32_t)nb;
+    prm.depth_last = (int32_t)(steps - (nb - 1) * D);
+    prm.debug_stall = debug_stall;
+    for (int k = 0; k < p->npts; ++k) {
+        prm.coef[k] = p->coef[k];
+        prm.coef_f[k] = (float)p->coef[k];
+    }
+    int occ = 0;
+    e = rs_occupancy(p, D, &occ);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (occ < 1) return EBISU_ERR_UNSUPPORTED;
+    int64_t grid = (int64_t)std::min(occ, q.ctas_per_sm) * dv.sms;
+    grid = std::min<int64_t>(grid, (prm.nitems + kRSWarps - 1) / kRSWarps);
+    e = rs_launch(p, D, prm, (int)grid, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return EBISU_OK;
+}
+
+}  // namespace ebisu
 
 extern "C" {
 
@@ -314,6 +443,7 @@ int ebisu_plan_create(int ndim, const int64_t* dims, int shape, int radius, cons
         best.threads = kThreads;
     }
     p->prm = best;
+    p->tb_prm = best;
     *out = p;
     return EBISU_OK;
 }
@@ -349,11 +479,39 @@ int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* q)
 {
     if (!plan || !q) return EBISU_ERR_INVALID_ARG;
     ebisu_params v = *q;
-    v.threads = kThreads;
+    if (v.fused_variant != 0 && v.fused_variant != 2) return EBISU_ERR_INVALID_ARG;
+    // the build whose parameters the tile and depth fields hold
+    const int build = (v.variant == 1) ? v.fused_variant : v.variant;
+    v.threads = (build == 2) ? kRSThreads : kThreads;
     if (v.ctas_per_sm == 0) v.ctas_per_sm = 1;
     const int rc = check_params(plan, v);
     if (rc != EBISU_OK) return rc;
+    if (v.variant == 2) {
+        RSLayout L;
+        rs_layout(plan, v, &L);
+        v.tile_x = L.S;  // derived: 128 - 2 * depth * radius
+        v.tile_y = 1;
+        v.tile_s = L.H;
+        v.fused_variant = 2;
+    } else if (build == 0) {
+        plan->tb_prm = v;
+        plan->tb_prm.variant = 0;
+        plan->tb_prm.fused_variant = 0;
+        if (v.variant == 0) v.fused_variant = 0;
+    }
     plan->prm = v;
+    return EBISU_OK;
+}
+
+int ebisu_plan_rs_depths(ebisu_plan_t plan, int* shallow, int* deep)
+{
+    if (!plan || !shallow || !deep) return EBISU_ERR_INVALID_ARG;
+    if (plan->ndim != 2) {
+        *shallow = *deep = 0;
+        return EBISU_OK;
+    }
+    *shallow = rs_depth((int)plan->esize, plan->shape, plan->radius, 0);
+    *deep = rs_depth((int)plan->esize, plan->shape, plan->radius, 1);
     return EBISU_OK;
 }
 
@@ -382,6 +540,7 @@ static int run_common(ebisu_plan_t p, const void* in, void* out, int64_t steps, 
         }
         return EBISU_OK;
     }
+    if (!naive && p->prm.variant == 2) return run_rs(p, in, out, steps, ws, st, debug_stall);
     if (naive || p->prm.variant == 1) {
         // one launch per step; buffers alternate so that the last lands in out
         const void* src = in;

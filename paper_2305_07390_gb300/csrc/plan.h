@@ -15,6 +15,7 @@ struct ebisu_plan_s {
     int npts = 0;
     double coef[ebisu::kMaxPoints] = {};
     ebisu_params prm{};
+    ebisu_params tb_prm{};  // shared-memory kernel parameters (batches and the server use them)
     // streaming coordinates (s, p1, p2); p1 is a dummy axis in 2D
     int64_t n[3] = {1, 1, 1};
     int64_t ext[3] = {1, 1, 1};  // stored extents
@@ -79,5 +80,13 @@ cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, cuda
 cudaError_t pad_copy(const ebisu_plan_s* p, const void* src, void* d0, void* d1, cudaStream_t st);
 
 int64_t wait_timeout_ns();
+
+// Register-streaming build (variant 2, 2D): strips of S columns, segments of H rows.
+struct RSLayout {
+    int S, H, nstrips, nsegs;
+};
+int rs_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L);
+cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int grid, cudaStream_t st);
+cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, int* blocks);
 
 }  // namespace ebisu

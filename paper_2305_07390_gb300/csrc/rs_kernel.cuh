@@ -1,0 +1,288 @@
+// rs_kernel.cuh -- register-streaming temporally blocked kernel (2D grids).
+//
+// The same method as tb_kernel.cuh (t Jacobi steps fused per temporal block,
+// tile by tile, the tile streamed along y and every time level kept on chip,
+// Sections 2.1 and 4), with the on-chip storage moved from shared memory to
+// registers and the tile narrowed to what one warp holds:
+//  * One warp owns a strip of 128 columns (lane l holds columns 4l .. 4l+3)
+//    and streams it down a segment of rows.  Each time level s < t keeps its
+//    last 2r+1 rows in registers (the circular multi-queue of Section 4.2,
+//    one queue per level, indexed by row mod 2r+1; the row loop is unrolled
+//    2r+1 times so every queue index is a compile-time register name).
+//  * Level s computes row y - s*r when level 0 receives row y: with one warp
+//    per strip no barrier separates the levels, so the lag is r per level
+//    (the shared-memory kernel needs r+1 to hide its per-plane barrier).
+//  * Horizontal neighbours come from the adjacent lanes by warp shuffles:
+//    star stencils shuffle the r edge cells of the centre row when they use
+//    it; box stencils keep every queued row widened by r cells per side,
+//    shuffled once when the row is produced.
+//  * Overlapped tiling (Section 2.1.2) at warp granularity: the valid part of
+//    a strip shrinks by r columns per level and side, so strips advance by
+//    S = 128 - 2*t*r columns; rows overlap the same way along y.
+//  * Level-0 rows are loaded PF rows ahead into registers (Section 4.3.1's
+//    prefetching, without a shared-memory stage).
+//  * Tiles of block b wait only for the (up to) eight neighbouring tiles of
+//    block b-1 -- the tiles whose outputs their inputs overlap -- through one
+//    completion counter per tile.  Those are also the only tiles of block b-1
+//    that read the region a tile of block b overwrites in the ping-pong
+//    buffer, so the same wait orders both hazards.  Items are popped in
+//    (block, tile) order and every warp of the grid is resident, so a wait
+//    only targets items already held by running warps: no deadlock.
+//  * Dirichlet pad cells keep their input value at every level (copied from
+//    the level below); periodic neighbours wrap when level 0 is loaded.
+#pragma once
+#include "common.h"
+#include "stencil.cuh"
+
+namespace ebisu {
+
+template <class T, int SHAPE, int R>
+struct RSGeom {
+    using C = typename DT<T>::C;
+    static constexpr int U = 2 * R + 1;                       // rows queued per level
+    static constexpr bool EXT = (SHAPE == kBox);              // rows stored with halo
+    static constexpr int RW = EXT ? 4 + 2 * R : 4;            // values per queued row
+    static constexpr int PF = (sizeof(C) == 8) ? 1 : U;       // level-0 rows in flight (divides U)
+    static constexpr int WORDS = (int)sizeof(C) / 4;
+    // registers a thread needs at depth D: the queues, the rows in flight,
+    // the star's widened centre row, the accumulators, and about 56 for
+    // addresses, loop state and the item's geometry (the 25-point box keeps
+    // more of its rows' values live across its 100 FMAs: found by compiling)
+    static constexpr int regs(int D)
+    {
+        return (D * U * RW + PF * RW + (EXT ? 0 : 4 + 2 * R) + 4) * WORDS + 56 + ((EXT && R == 2) ? 48 : 0);
+    }
+    static constexpr int minb(int D)
+    {
+        const int e = (regs(D) + 7) & ~7;
+        const int b = 65536 / (kRSThreads * e);
+        return b < 1 ? 1 : (b > 8 ? 8 : b);
+    }
+};
+
+template <class T, int SHAPE, int R, int D>
+__global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D))
+    rs_kernel(const __grid_constant__ RSParams prm)
+{
+    using G = RSGeom<T, SHAPE, R>;
+    using Dt = DT<T>;
+    using C = typename Dt::C;
+    using St = Stencil<2, SHAPE, R>;
+    constexpr int P = St::P;
+    constexpr int U = G::U;
+    constexpr int RW = G::RW;
+    constexpr int PF = G::PF;
+    constexpr bool EXT = G::EXT;
+    constexpr int X0 = EXT ? R : 0;  // position of cell 0 in a queued row
+    constexpr auto OFF = St::kOff;   // ds = row offset, d2 = column offset
+    static_assert(U % PF == 0, "prefetch slots must divide the unrolled row count");
+    static_assert(R <= 3 && 2 * D * R < kRSCols, "strip too narrow for this depth");
+    constexpr unsigned FULL = 0xffffffffu;
+
+    const int lane = threadIdx.x & 31;
+    Control* const ctl = prm.ctl;
+    const int64_t ntiles = (int64_t)prm.nstrips * prm.nsegs;
+    const bool per = prm.periodic != 0;
+    const int64_t n0 = prm.n0;
+    const int n2 = prm.n2;
+    const int pad = prm.pad;
+    const int64_t lds = prm.lds;
+    // coefficients stay in the parameter bank: FMAs take them as operands
+    auto coef = [&](int k) -> C {
+        if constexpr (sizeof(C) == 8) return prm.coef[k];
+        else return prm.coef_f[k];
+    };
+
+    C ring[D][U][RW];  // levels 0 .. D-1; level D goes to global memory
+    C stage[PF][RW];   // level-0 rows in flight
+
+    for (;;) {
+        // ---- pop an item: (temporal block, segment, strip) --------------------
+        long long it = -1;
+        if (lane == 0 && *(volatile int*)&ctl->status == 0) it = (long long)atomicAdd(&ctl->next_item, 1u);
+        it = __shfl_sync(FULL, it, 0);
+        if (it < 0 || it >= prm.nitems) return;
+        const int blk = (int)(it / ntiles);
+        const int tile = (int)(it - (long long)blk * ntiles);
+        const int seg = tile / prm.nstrips;
+        const int strip = tile - seg * prm.nstrips;
+
+        // ---- wait for the neighbouring tiles of the previous block -------------
+        // lanes 0..8 each watch one of the 3 x 3 neighbours (bounded waits)
+        int ok = 1;
+        if (lane < 9 && (blk > 0 || prm.debug_stall)) {
+            int sg = seg + lane / 3 - 1, sx = strip + lane % 3 - 1;
+            bool exists = true;
+            if (per) {
+                sg = (sg + prm.nsegs) % prm.nsegs;
+                sx = (sx + prm.nstrips) % prm.nstrips;
+            } else {
+                exists = sg >= 0 && sg < prm.nsegs && sx >= 0 && sx < prm.nstrips;
+            }
+            if (exists) {
+                const unsigned target = (unsigned)blk + (prm.debug_stall ? 1u : 0u);
+                const unsigned* cnt = &ctl->done[(int64_t)sg * prm.nstrips + sx];
+                if (ld_acquire_u32(cnt) < target) {
+                    const uint64_t t0 = global_ns();
+                    unsigned ns = 32;
+                    while (ld_acquire_u32(cnt) < target) {
+                        if (*(volatile int*)&ctl->status != 0) { ok = 0; break; }
+                        if (global_ns() - t0 > (uint64_t)prm.timeout_ns) {
+                            atomicCAS(&ctl->status, 0, 6 /* EBISU_ERR_TIMEOUT */);
+                            atomicExch(&ctl->wait_where, (unsigned)it);
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(ns);
+                        ns = ns < 1024 ? ns * 2 : ns;
+                    }
+                }
+            }
+        }
+        if (!__all_sync(FULL, ok)) return;
+
+        // ---- geometry ------------------------------------------------------------
+        const bool lastb = (blk == prm.nblocks - 1);
+        const int deff = lastb ? prm.depth_last : D;  // levels above deff pass values through
+        const bool dst_is_out = ((prm.nblocks - 1 - blk) & 1) == 0;
+        T* const dst = reinterpret_cast<T*>(dst_is_out ? prm.out : prm.ws);
+        const T* const src = (blk == 0) ? reinterpret_cast<const T*>(prm.src0)
+                                        : reinterpret_cast<const T*>(dst_is_out ? prm.ws : prm.out);
+        const int xs = strip * prm.S;          // first output column of the strip
+        const int xe = min(xs + prm.S, n2);    // end of the output columns
+        const int cb = xs - D * R + 4 * lane;  // column of this lane's cell 0
+        // rows (int: the host keeps n0 + 2 * pad below 2^31)
+        const int ya = seg * prm.H;
+        const int yb = min(ya + prm.H, (int)n0);
+        const int n0i = (int)n0;
+        // rows of level s: [ya - r(D-s), yb + r(D-s)), clipped to the padded
+        // grid; level 0 is loaded over [lo0, hi0)
+        const int lo0 = per ? ya - R * D : max(ya - R * D, -pad);
+        const int hi0 = per ? yb + R * D : min(yb + R * D, n0i + pad);
+        const int niter = yb + D * R - lo0;  // level D's last row arrives last
+
+        // loaded columns cb - X0 .. cb - X0 + RW - 1: which exist (Dirichlet:
+        // inside the padded row), and whether they are one contiguous run
+        // (periodic: no wrap inside this lane's columns)
+        const int c0 = cb - X0;
+        unsigned lvm = 0;
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+            const int c = c0 + q;
+            if (per || ((c >= -pad) && (c < n2 + pad))) lvm |= 1u << q;
+        }
+        const int cw0 = per ? (c0 < 0 ? c0 + n2 : (c0 >= n2 ? c0 - n2 : c0)) : 0;  // wrapped c0
+        const bool contig = cw0 + RW <= n2;
+        unsigned padm = 0, outm = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int c = cb + m;
+            if (!per && (c < 0 || c >= n2)) padm |= 1u << m;
+            if (c >= xs && c < xe) outm |= 1u << m;
+        }
+
+        auto load_row = [&](C(&v)[RW], int y) {
+            if (y >= hi0) return;  // below the region: never used
+            if (per) {
+                // one wrap at most: the host keeps n0 >= 64 and n2 >= 128
+                const int yw = (y < 0) ? y + n0i : (y >= n0i ? y - n0i : y);
+                const T* rp = src + (int64_t)yw * lds;
+                if (contig) {
+#pragma unroll
+                    for (int q = 0; q < RW; ++q) v[q] = Dt::load(rp + cw0 + q);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < RW; ++q) {
+                        const int c = cw0 + q;
+                        v[q] = Dt::load(rp + (c >= n2 ? c - n2 : c));
+                    }
+                }
+            } else {
+                const T* rp = src + (int64_t)(y + pad) * lds + (c0 + pad);
+#pragma unroll
+                for (int q = 0; q < RW; ++q) v[q] = ((lvm >> q) & 1u) ? Dt::load(rp + q) : C(0);
+            }
+        };
+
+#pragma unroll
+        for (int q = 0; q < PF; ++q) load_row(stage[q], lo0 + q);
+
+        // ---- stream the strip ----------------------------------------------------
+        // The body is branch-free: every level computes a row at every step.
+        // A row outside its level's region (the ramp at the segment's ends,
+        // rows past the padded grid, the steps after the last) holds garbage
+        // that no kept value depends on: a row y of level s+1 inside its
+        // region reads rows y-r .. y+r of level s, all inside level s's
+        // region.  Only level-t rows inside the segment are stored.
+        for (int j0 = 0; j0 < niter; j0 += U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int yi = lo0 + j0 + u;  // level-0 row arriving now
+#pragma unroll
+                for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
+                load_row(stage[u % PF], yi + PF);
+#pragma unroll
+                for (int s = 1; s <= D; ++s) {
+                    const int y = yi - s * R;                   // row of level s computed now
+                    const int cs = ((u - s * R) % U + U) % U;   // queue slot of row y
+                    // pad rows and the levels past the last block's depth keep
+                    // the value below; pad columns likewise
+                    const bool copy = (s > deff) || (!per && (y < 0 || y >= n0i));
+                    const unsigned keep = copy ? 0xfu : padm;
+                    C e[4 + 2 * R];  // star: centre row with r cells of halo per side
+                    if constexpr (!EXT) {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) e[R + m] = ring[s - 1][cs][m];
+#pragma unroll
+                        for (int i = 0; i < R; ++i) {
+                            e[i] = __shfl_up_sync(FULL, ring[s - 1][cs][4 - R + i], 1);
+                            e[R + 4 + i] = __shfl_down_sync(FULL, ring[s - 1][cs][i], 1);
+                        }
+                    }
+                    C acc[4];
+#pragma unroll
+                    for (int k = 0; k < P; ++k) {
+                        const int dy = OFF.ds[k], dx = OFF.d2[k];
+                        const int rs = (cs + dy + U) % U;
+                        const C ck = coef(k);
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            C v;
+                            if constexpr (EXT) v = ring[s - 1][rs][X0 + m + dx];
+                            else v = (dy == 0) ? e[R + m + dx] : ring[s - 1][rs][m];
+                            acc[m] = (k == 0) ? Dt::mul(ck, v) : Dt::fma(ck, v, acc[m]);
+                        }
+                    }
+                    C o[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m)
+                        o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m] : Dt::widen(Dt::narrow(acc[m]));
+                    if (s < D) {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) ring[s][cs][X0 + m] = o[m];
+                        if constexpr (EXT) {
+#pragma unroll
+                            for (int i = 0; i < R; ++i) {
+                                ring[s][cs][i] = __shfl_up_sync(FULL, o[4 - R + i], 1);
+                                ring[s][cs][X0 + 4 + i] = __shfl_down_sync(FULL, o[i], 1);
+                            }
+                        }
+                    } else {
+                        const unsigned st = (y >= ya && y < yb) ? outm : 0u;
+                        T* const rp = dst + (per ? (int64_t)y * lds : (int64_t)(y + pad) * lds + pad) + cb;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m)
+                            if ((st >> m) & 1u) rp[m] = Dt::narrow(o[m]);
+                    }
+                }
+            }
+        }
+
+        // ---- publish completion of this tile -------------------------------------
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) red_release_add_u32(&ctl->done[tile], 1u);
+    }
+}
+
+}  // namespace ebisu

@@ -299,14 +299,53 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
     naive.variant = 1;
     cand.push_back(naive);
     ++n;
+    // The register-streaming build (2D): both built depths, segments sized so
+    // that one temporal block has about 1, 2 or 4 tiles per resident warp.
+    if (plan->ndim == 2) {
+        const DeviceInfo& dv = device_info();
+        for (int which = 0; which < 2; ++which) {
+            const int D = rs_depth((int)plan->esize, plan->shape, plan->radius, which);
+            if (which == 1 && D == rs_depth((int)plan->esize, plan->shape, plan->radius, 0)) break;
+            int occ = 0;
+            if (rs_occupancy(plan, D, &occ) != cudaSuccess || occ < 1) {
+                cudaGetLastError();
+                continue;
+            }
+            const int64_t warps = (int64_t)occ * dv.sms * kRSWarps;
+            const int64_t S = kRSCols - 2LL * D * plan->radius;
+            const int64_t ns = (plan->n[2] + S - 1) / S;
+            int64_t lastH = -1;
+            for (int k : {1, 2, 4}) {
+                const int64_t ng = std::max<int64_t>(1, (k * warps + ns - 1) / ns);
+                const int64_t H = (plan->n[0] + ng - 1) / ng;
+                if (H == lastH) continue;
+                lastH = H;
+                ebisu_params q{};
+                q.variant = 2;
+                q.depth = D;
+                q.tile_s = (int32_t)H;
+                q.ctas_per_sm = occ;
+                q.threads = kRSThreads;
+                RSLayout L;
+                if (rs_layout(plan, q, &L) != EBISU_OK) continue;
+                q.tile_x = L.S;
+                q.tile_y = 1;
+                cand.push_back(q);
+                ++n;
+            }
+        }
+    }
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail_cuda(cudaGetLastError());
     const ebisu_params saved = plan->prm;
+    const ebisu_params saved_tb = plan->tb_prm;
     double best = 1e300;
     ebisu_params bestp = saved;
-    ebisu_params best_blocked = cand[0];
+    ebisu_params best_blocked = cand[0];  // shared-memory build (variant 0)
     double best_blocked_ms = 1e300;
+    ebisu_params best_fused = cand[0];    // variant 0 or 2
+    double best_fused_ms = 1e300;
     int rc = EBISU_OK;
     for (int i = 0; i < n; ++i) {
         plan->prm = cand[i];
@@ -328,16 +367,26 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
             best_blocked_ms = ms;
             best_blocked = cand[i];
         }
+        if (cand[i].variant != 1 && ms < best_fused_ms) {
+            best_fused_ms = ms;
+            best_fused = cand[i];
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc == EBISU_OK) {
-        // keep the best fused-kernel parameters (batches and the server use
-        // them) and record which kernel won in `variant`
-        plan->prm = best_blocked;
-        plan->prm.variant = bestp.variant;
+        // keep the best shared-memory-kernel parameters (batches and the
+        // server use them) and the best temporally blocked build's
+        // parameters; `variant` says which kernel won (1: the one-step
+        // kernel, whose runs ignore the other fields)
+        plan->tb_prm = best_blocked;
+        plan->tb_prm.fused_variant = 0;
+        plan->prm = best_fused;
+        plan->prm.fused_variant = best_fused.variant;
+        if (bestp.variant == 1) plan->prm.variant = 1;
     } else {
         plan->prm = saved;
+        plan->tb_prm = saved_tb;
     }
     if (best_ms) *best_ms = best;
     return rc;

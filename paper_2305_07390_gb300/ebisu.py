@@ -37,10 +37,10 @@ class EbisuError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32), ("tile_s", ctypes.c_int32),
                 ("depth", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("threads", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("variant", ctypes.c_int32), ("fused_variant", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class ModelIn(ctypes.Structure):
@@ -76,6 +76,7 @@ SIGNATURES = {
     "ebisu_plan_grid_elems": (_I, [_P, ctypes.POINTER(_I64)]),
     "ebisu_plan_get_params": (_I, [_P, ctypes.POINTER(Params)]),
     "ebisu_plan_set_params": (_I, [_P, ctypes.POINTER(Params)]),
+    "ebisu_plan_rs_depths": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "ebisu_plan_workspace_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "ebisu_run": (_I, [_P, _P, _P, _I64, _P, _P]),
     "ebisu_run_naive": (_I, [_P, _P, _P, _I64, _P, _P]),
@@ -255,6 +256,12 @@ class Plan:
         for k, v in kw.items():
             setattr(p, k, int(v))
         _check(lib().ebisu_plan_set_params(self.h, ctypes.byref(p)), "ebisu_plan_set_params")
+
+    def rs_depths(self):
+        """Temporal depths built for the register-streaming kernel (variant 2)."""
+        a, b = _I(), _I()
+        _check(lib().ebisu_plan_rs_depths(self.h, ctypes.byref(a), ctypes.byref(b)), "ebisu_plan_rs_depths")
+        return a.value, b.value
 
     def model(self):
         pred, bound, valid = _D(), _I(), _D()

@@ -85,3 +85,35 @@ def test_run_argument_errors_need_no_device():
     # unaligned workspace
     assert lib.ebisu_run(p.h, ctypes.c_void_p(256), ctypes.c_void_p(512), 1, ctypes.c_void_p(1000),
                          None) == ebisu.ERR_INVALID_ARG
+
+
+def test_register_streaming_params():
+    """Variant 2 (register streaming, 2D): depths, derived strip width and
+    the host-side validity rules, checked without a device."""
+    p = ebisu.Plan(2, (1000, 1000), 0, 1, [0.2] * 5, ebisu.F32, ebisu.DIRICHLET)
+    lo, hi = p.rs_depths()
+    assert 1 <= lo <= hi
+    p.set_params(variant=2, depth=hi, tile_s=100, ctas_per_sm=2)
+    q = p.params()
+    assert (q.variant, q.depth, q.tile_x, q.tile_s, q.threads) == (2, hi, 128 - 2 * hi, 100, 128)
+    for bad in [dict(variant=2, depth=hi + 1),            # not a built depth
+                dict(variant=2, depth=hi, tile_s=hi - 1),  # segment shorter than depth * radius
+                dict(variant=3)]:
+        with pytest.raises(ebisu.EbisuError):
+            p.set_params(**bad)
+    # too many tiles for the per-tile counters
+    big = ebisu.Plan(2, (40000, 2000), 0, 1, [0.2] * 5, ebisu.F32, ebisu.DIRICHLET)
+    with pytest.raises(ebisu.EbisuError) as ei:
+        big.set_params(variant=2, depth=lo, tile_s=lo)
+    assert ei.value.code == ebisu.ERR_UNSUPPORTED
+    # no 3D build; periodic grids must be at least 64 x 136
+    p3 = ebisu.Plan(3, (20, 20, 20), 0, 1, [0.1] * 7, ebisu.F32, ebisu.DIRICHLET)
+    assert p3.rs_depths() == (0, 0)
+    with pytest.raises(ebisu.EbisuError):
+        p3.set_params(variant=2, depth=4)
+    pp = ebisu.Plan(2, (100, 100), 0, 1, [0.2] * 5, ebisu.F32, ebisu.PERIODIC)
+    with pytest.raises(ebisu.EbisuError):
+        pp.set_params(variant=2, depth=pp.rs_depths()[0])
+    # FP64 builds shallow depths only (its FMA pipe, not HBM, bounds it)
+    p64 = ebisu.Plan(2, (500, 500), 1, 2, [0.04] * 25, ebisu.F64, ebisu.DIRICHLET)
+    assert p64.rs_depths() == (1, 1)

@@ -1,0 +1,153 @@
+"""GPU parity of the register-streaming temporally blocked kernel (variant 2).
+
+Every 2D stencil, storage type, boundary and both built temporal depths,
+against the FP64 oracle (relative L-infinity: FP64 1e-12, FP32 1e-5,
+BF16 2e-2) and bit-exact against the naive one-step kernel (same per-cell
+FMA order).  The grids span several 128-column strips and several segments,
+with ragged last strips and segments, and step counts that leave a partial
+last temporal block.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2305_07390_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5, 2: 2e-2}
+STENCILS_2D = [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2)]
+
+
+def _eb():
+    from paper_2305_07390_gb300 import ebisu
+    return ebisu
+
+
+def device_problem(eb, dims, shape, r, dtype, boundary, seed):
+    g, c = synth.problem(2, dims, shape, r, boundary, seed=seed)
+    x = torch.from_numpy(g).to(eb.torch_dtype(dtype)).cuda()
+    held = x.double().cpu().numpy()
+    c_held = c if dtype == eb.F64 else c.astype(np.float32).astype(np.float64)
+    return x, held, c, c_held
+
+
+def rs_plan(eb, dims, shape, r, c, dtype, boundary, which, tile_s):
+    plan = eb.Plan(2, dims, shape, r, c, dtype, boundary)
+    d = plan.rs_depths()[which]
+    plan.set_params(variant=2, depth=d, tile_s=tile_s, ctas_per_sm=8)
+    return plan, d
+
+
+def run(plan, x, steps, naive=False):
+    ws = plan.workspace()
+    y = torch.empty_like(x)
+    plan.run(x, y, steps, ws, naive=naive)
+    assert plan.sync(ws) == 0
+    return y
+
+
+def check_pad(y, held, pad):
+    m = np.ones(held.shape, bool)
+    m[pad:-pad, pad:-pad] = False
+    assert np.array_equal(y.double().cpu().numpy()[m], held[m])
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+@pytest.mark.parametrize("shape,r", STENCILS_2D)
+@pytest.mark.parametrize("boundary", [0, 1])
+@pytest.mark.parametrize("which", [0, 1])
+def test_rs_parity(shape, r, dtype, boundary, which):
+    eb = _eb()
+    dims = (203, 517)
+    x, held, c, c_held = device_problem(eb, dims, shape, r, dtype, boundary, seed=300 + 7 * r + shape)
+    plan, d = rs_plan(eb, dims, shape, r, c, dtype, boundary, which, tile_s=37)
+    p = plan.params()
+    assert p.variant == 2 and p.tile_x == 128 - 2 * d * r and p.tile_s == 37
+    steps = 2 * d + 1  # a partial last block
+    y = run(plan, x, steps)
+    yn = run(plan, x, steps, naive=True)
+    assert torch.equal(y, yn), "register-streaming and naive kernels differ"
+    ref = oracle.run(held, shape, r, c_held, boundary, steps)
+    pad = r if boundary == 0 else 0
+    assert oracle.rel_linf(y.double().cpu().numpy(), ref, pad) <= TOL[dtype]
+    if boundary == 0:
+        check_pad(y, held, pad)
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3, 7, 8, 9, 17])
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_rs_step_counts(steps, dtype):
+    eb = _eb()
+    dims = (150, 260)
+    x, held, c, c_held = device_problem(eb, dims, 0, 1, dtype, 0, seed=11)
+    plan, d = rs_plan(eb, dims, 0, 1, c, dtype, 0, 1, tile_s=40)
+    y = run(plan, x, steps)
+    assert torch.equal(y, run(plan, x, steps, naive=True))
+    ref = oracle.run(held, 0, 1, c_held, 0, steps)
+    assert oracle.rel_linf(y.double().cpu().numpy(), ref, 1) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("dims,tile_s", [((9, 50), 0), ((64, 120), 8), ((300, 140), 300), ((70, 1000), 9)])
+@pytest.mark.parametrize("shape,r", [(0, 1), (1, 2)])
+def test_rs_shapes(dims, tile_s, shape, r):
+    """A strip wider than the grid, segments exactly depth*radius rows, one
+    segment over the whole height, many narrow segments."""
+    eb = _eb()
+    x, held, c, c_held = device_problem(eb, dims, shape, r, eb.F32, 0, seed=12)
+    plan = eb.Plan(2, dims, shape, r, c, eb.F32, 0)
+    d = plan.rs_depths()[0]
+    ts = tile_s if tile_s else 0
+    if ts and ts < d * r and ts < dims[0]:
+        ts = d * r
+    plan.set_params(variant=2, depth=d, tile_s=ts, ctas_per_sm=4)
+    steps = d + 2
+    y = run(plan, x, steps)
+    assert torch.equal(y, run(plan, x, steps, naive=True))
+    ref = oracle.run(held, shape, r, c_held, 0, steps)
+    assert oracle.rel_linf(y.double().cpu().numpy(), ref, r) <= TOL[1]
+
+
+@pytest.mark.parametrize("steps", [1, 4, 5, 8, 9])
+def test_rs_in_place(steps):
+    eb = _eb()
+    dims = (96, 300)
+    x, held, c, c_held = device_problem(eb, dims, 0, 1, eb.F32, 0, seed=13)
+    plan, d = rs_plan(eb, dims, 0, 1, c, eb.F32, 0, 0, tile_s=24)
+    ws = plan.workspace()
+    y = x.clone()
+    plan.run(y, y, steps, ws)
+    assert plan.sync(ws) == 0
+    ref = oracle.run(held, 0, 1, c_held, 0, steps)
+    assert oracle.rel_linf(y.double().cpu().numpy(), ref, 1) <= TOL[1]
+
+
+def test_rs_wait_timeout_reports_status(monkeypatch):
+    eb = _eb()
+    monkeypatch.setenv("EBISU_WAIT_TIMEOUT_MS", "200")
+    dims = (64, 200)
+    x, held, c, _ = device_problem(eb, dims, 0, 1, eb.F64, 0, seed=14)
+    plan, d = rs_plan(eb, dims, 0, 1, c, eb.F64, 0, 0, tile_s=32)
+    ws = plan.workspace()
+    y = torch.empty_like(x)
+    plan.run_stalled(x, y, 3, ws)
+    assert plan.sync(ws) == eb.ERR_TIMEOUT
+    # the context stays usable: a normal run afterwards succeeds
+    plan.run(x, y, 3, ws)
+    assert plan.sync(ws) == 0
+
+
+def test_rs_tuner_may_pick_it():
+    """The tuner times the register-streaming build beside the others; the
+    plan then runs whichever won, and the result matches the naive kernel."""
+    eb = _eb()
+    dims = (1024, 1024)
+    x, held, c, _ = device_problem(eb, dims, 0, 1, eb.F32, 0, seed=15)
+    plan = eb.Plan(2, dims, 0, 1, c, eb.F32, 0)
+    ws = plan.workspace()
+    y = torch.empty_like(x)
+    plan.tune(x, y, 16, ws, max_candidates=4)
+    assert plan.params().variant in (0, 1, 2)
+    y = run(plan, x, 21)
+    assert torch.equal(y, run(plan, x, 21, naive=True))
