@@ -32,6 +32,28 @@ STENCILS = [("star", 0, 1), ("star", 0, 2), ("star", 0, 3), ("box", 1, 1), ("box
 FP64_PEAK_FLOPS = 1.25e12  # nominal GB300 FP64 rate (vector = tensor on this part)
 
 
+def hbm_peak():
+    """Measured copy bandwidth (bytes/s) of this machine's GPUs, else the
+    profiling recipe's fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]) * 1e9, "measured"
+    except (OSError, KeyError, ValueError):
+        return 6.8e12, "fallback"
+
+
+def stencil_roofline(rate, points, esize, depth, fp_flops, hbm):
+    """Roofline of a temporally blocked solve: the lower of HBM bandwidth over
+    the bytes a cell costs per temporal block (one read and one write of the
+    stored value per `depth` steps) and the FMA pipe's peak over 2P flops per
+    cell update."""
+    hbm_bound = hbm / (2.0 * esize / depth)
+    fp_bound = fp_flops / (2.0 * points)
+    roof = min(hbm_bound, fp_bound)
+    return dict(bound="hbm" if hbm_bound < fp_bound else "alu", roof_cell_updates_per_s=roof,
+                frac=rate / roof)
+
+
 VARIANT_NAMES = {0: "fused (shared-memory queues)", 1: "naive", 2: "fused (register streaming)"}
 KERNEL_NAMES = {0: "tb_kernel", 1: "naive_kernel", 2: "rs_kernel"}
 
@@ -440,7 +462,7 @@ def main():
     # Section 6's fine-tuning: the cost model ranks parameter sets, a short
     # timed run of the best few on this grid picks one (outside the timed region)
     for p in probs:
-        p["plan"].tune(p["x"], p["y"], min(steps, 16), p["ws"], max_candidates=args.tune)
+        p["plan"].tune(p["x"], p["y"], min(steps, 48), p["ws"], max_candidates=args.tune)
         q = p["plan"].params()
         p["tuned_variant"] = q.variant
         if q.variant == 1:  # the headline times a temporally blocked build
@@ -531,7 +553,60 @@ def main():
         e2e_ms.append(a.elapsed_time(b))
     e2e_val = upd_per_step * ws_n / (max(e2e_ms) * 1e-3)
 
+    # the FP32- and BF16-storage forms of the same solves (FP32 arithmetic):
+    # rate, speedup over the FP64 path, and error against the FP64 result
+    # (itself checked against the oracle by the full-size parity tests)
+    forms = []
+    for dt, dname in ((ebisu.F32, "f32"), (ebisu.BF16, "bf16")):
+        rows = []
+        for p, d in zip(probs, per):
+            plan = ebisu.Plan(2, (N, N), p["shape"], p["r"], p["plan"].coeffs, dt, ebisu.DIRICHLET)
+            xl = p["x"].to(ebisu.torch_dtype(dt))
+            yl = torch.empty_like(xl)
+            wsl = plan.workspace()
+            plan.tune(xl, yl, min(steps, 48), wsl, max_candidates=args.tune)
+            q = plan.params()
+            tuned = q.variant
+            if q.variant == 1:
+                plan.set_params(variant=q.fused_variant)
+            plan.run(xl, yl, steps, wsl, stream=sh)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.run(xl, yl, steps, wsl, stream=sh)
+            b.record(stream)
+            b.synchronize()
+            rc = plan.sync(wsl)
+            assert rc == 0, ebisu.status_string(rc)
+            ms = a.elapsed_time(b)
+            rr = p["r"]
+            ref = p["y"][rr:-rr, rr:-rr]
+            err = float((yl[rr:-rr, rr:-rr].double() - ref).abs().max() / ref.abs().max())
+            a.record(stream)
+            plan.run(xl, yl, min(steps, 100), wsl, stream=sh, naive=True)
+            b.record(stream)
+            b.synchronize()
+            naive_rate = cells * min(steps, 100) / (a.elapsed_time(b) * 1e-3)
+            rate = cells * steps / (ms * 1e-3)
+            rows.append(dict(stencil=p["name"], cell_updates_per_s=rate,
+                             speedup_vs_fp64=rate / d["cell_updates_per_s"],
+                             naive_cell_updates_per_s=naive_rate, speedup_vs_naive=rate / naive_rate,
+                             rel_linf_vs_fp64=err, tuner_preferred=VARIANT_NAMES[tuned],
+                             kernel=KERNEL_NAMES[plan.params().variant], params=plan.params().as_dict()))
+            del xl, yl, wsl, plan
+        torch.cuda.empty_cache()
+        forms.append(dict(dtype=dname, per_stencil=rows,
+                          set_cell_updates_per_s=len(rows) * cells * steps /
+                          sum(cells * steps / r_["cell_updates_per_s"] for r_ in rows)))
+
     probe = ebisu.ebisu_probe_device()
+    hbm, hbm_src = hbm_peak()
+    for f in forms:
+        es = 4 if f["dtype"] == "f32" else 2
+        for r_, p in zip(f["per_stencil"], probs):
+            r_["roofline"] = stencil_roofline(r_["cell_updates_per_s"], p["P"], es, r_["params"]["depth"],
+                                              probe["f32_flops"], hbm)
+        f["roofline_peaks"] = {"hbm_bytes_per_s": hbm, "hbm_source": hbm_src,
+                               "fp32_flops": probe["f32_flops"], "fp32_source": "live probe (FMA loop)"}
     cpu = None
     if rank == 0 and ws_n >= 1 and not args.no_cpu and ws_n == 1:
         cpu = cpu_baseline()
@@ -551,9 +626,12 @@ def main():
                      "peak_source": "nominal FP64 rate of the profiling recipe's table; live probe "
                                     f"{probe['f64_flops'] / 1e12:.3f} TFLOP/s"},
         "per_stencil": per,
+        "precision_forms": forms,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": max(e2e_ms)},
-        "gpu_launches": len(probs) * args.steps,
+        # per solve: the blocked kernel, plus the pad copy the register-
+        # streaming build launches before it (Dirichlet)
+        "gpu_launches": args.steps * sum(1 + (p["plan"].params().variant == 2) for p in probs),
         "clocks": clk,
     }
     if cpu is not None:

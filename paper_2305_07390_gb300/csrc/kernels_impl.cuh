@@ -11,9 +11,14 @@
 namespace ebisu {
 
 // ---------------------------------------------------------------------------
-// Naive one-step kernel: one thread per interior cell, neighbours read from
-// global memory (read-only path), same canonical FMA chain as the blocked
-// kernel.  This is the "one time step per launch" reference GPU path.
+// Naive one-step kernel: one thread per interior cell of each of kNaiveRows
+// rows (2D: rows 8 apart, so a warp's loads stay coalesced; 3D: consecutive
+// planes), neighbours read from global memory (read-only path), same
+// canonical FMA chain as the blocked kernels.  This is the "one time step per
+// launch" reference GPU path; several cells per thread keep enough loads in
+// flight to stream at the memory bandwidth.
+
+constexpr int kNaiveRows = 4;
 
 template <class T, int DIM, int SHAPE, int R>
 __global__ void __launch_bounds__(256) naive_kernel(const T* __restrict__ src, T* __restrict__ dst,
@@ -28,8 +33,7 @@ __global__ void __launch_bounds__(256) naive_kernel(const T* __restrict__ src, T
     const int n1 = (int)a.n[1], n2 = (int)a.n[2];
     const int q2 = blockIdx.x * 32 + threadIdx.x;
     const int q1 = (DIM == 3) ? (int)(blockIdx.y * 8 + threadIdx.y) : 0;
-    const int64_t ps = (DIM == 3) ? (int64_t)blockIdx.z : (int64_t)blockIdx.y * 8 + threadIdx.y;
-    if (q2 >= n2 || q1 >= n1 || ps >= n0) return;
+    if (q2 >= n2 || q1 >= n1) return;
     const int pad = a.pad, pad1 = (DIM == 3) ? a.pad : 0;
     const int64_t lds = a.lds, ld1 = a.ld1;
     // coefficients already in the accumulation type: a per-cell FP64 -> FP32
@@ -38,26 +42,34 @@ __global__ void __launch_bounds__(256) naive_kernel(const T* __restrict__ src, T
         if constexpr (std::is_same<C, double>::value) return a.coef[k];
         else return a.coef_f[k];
     };
-    C acc;
-    if (a.periodic) {
-        auto at = [&](int k) -> C {
-            const int64_t s_ = wrap_idx(ps + OFF.ds[k], n0);
-            const int64_t y_ = (DIM == 3) ? wrap_idx(q1 + OFF.d1[k], n1) : 0;
-            const int64_t x_ = wrap_idx(q2 + OFF.d2[k], n2);
-            return D::load_ro(src + s_ * lds + y_ * ld1 + x_);
-        };
-        acc = D::mul(cf(0), at(0));
+    // unrolled: the rows' loads are all in flight together (at one cell per
+    // thread the kernel is bound by memory latency, not bandwidth)
 #pragma unroll
-        for (int k = 1; k < P; ++k) acc = D::fma(cf(k), at(k), acc);
-        dst[ps * lds + (int64_t)q1 * ld1 + q2] = D::narrow(acc);
-    } else {
-        const int64_t c = (ps + pad) * lds + (int64_t)(q1 + pad1) * ld1 + (q2 + pad);
-        const T* p = src + c;
-        auto at = [&](int k) -> C { return D::load_ro(p + OFF.ds[k] * lds + OFF.d1[k] * ld1 + OFF.d2[k]); };
-        acc = D::mul(cf(0), at(0));
+    for (int i = 0; i < kNaiveRows; ++i) {
+        const int64_t ps = (DIM == 3) ? (int64_t)blockIdx.z * kNaiveRows + i
+                                      : ((int64_t)blockIdx.y * kNaiveRows + i) * 8 + threadIdx.y;
+        if (ps >= n0) return;
+        C acc;
+        if (a.periodic) {
+            auto at = [&](int k) -> C {
+                const int64_t s_ = wrap_idx(ps + OFF.ds[k], n0);
+                const int64_t y_ = (DIM == 3) ? wrap_idx(q1 + OFF.d1[k], n1) : 0;
+                const int64_t x_ = wrap_idx(q2 + OFF.d2[k], n2);
+                return D::load_ro(src + s_ * lds + y_ * ld1 + x_);
+            };
+            acc = D::mul(cf(0), at(0));
 #pragma unroll
-        for (int k = 1; k < P; ++k) acc = D::fma(cf(k), at(k), acc);
-        dst[c] = D::narrow(acc);
+            for (int k = 1; k < P; ++k) acc = D::fma(cf(k), at(k), acc);
+            dst[ps * lds + (int64_t)q1 * ld1 + q2] = D::narrow(acc);
+        } else {
+            const int64_t c = (ps + pad) * lds + (int64_t)(q1 + pad1) * ld1 + (q2 + pad);
+            const T* p = src + c;
+            auto at = [&](int k) -> C { return D::load_ro(p + OFF.ds[k] * lds + OFF.d1[k] * ld1 + OFF.d2[k]); };
+            acc = D::mul(cf(0), at(0));
+#pragma unroll
+            for (int k = 1; k < P; ++k) acc = D::fma(cf(k), at(k), acc);
+            dst[c] = D::narrow(acc);
+        }
     }
 }
 
@@ -258,9 +270,9 @@ static cudaError_t naive_launch_t(int dim, int shape, int r, const void* src, vo
     dim3 grid((unsigned)((p.n[2] + 31) / 32), 1, 1);
     if (dim == 3) {
         grid.y = (unsigned)((p.n[1] + 7) / 8);
-        grid.z = (unsigned)p.n[0];
+        grid.z = (unsigned)((p.n[0] + kNaiveRows - 1) / kNaiveRows);
     } else {
-        grid.y = (unsigned)((p.n[0] + 7) / 8);
+        grid.y = (unsigned)((p.n[0] + 8 * kNaiveRows - 1) / (8 * kNaiveRows));
     }
     if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
     void* args[] = {(void*)&src, (void*)&dst, (void*)&p};

@@ -31,6 +31,8 @@
 //  * Dirichlet pad cells keep their input value at every level (copied from
 //    the level below); periodic neighbours wrap when level 0 is loaded.
 #pragma once
+#include <type_traits>
+
 #include "common.h"
 #include "stencil.cuh"
 
@@ -180,11 +182,26 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D))
             if (!per && (c < 0 || c >= n2)) padm |= 1u << m;
             if (c >= xs && c < xe) outm |= 1u << m;
         }
+        // Most tiles touch no boundary and belong to a full-depth block.  For
+        // the short FP32/BF16 stencils (5 and 9 points) those run a lean copy
+        // of the loop without pad, copy or wrap handling; everything else
+        // runs the general loop.  For FP64 (FMA-pipe bound) and the 13- and
+        // 25-point stencils a second copy of the loop only costs registers
+        // (measured).  Each copy's row body is branch-free, so the compiler
+        // can interleave the levels' instructions freely.
+        constexpr bool kLean = (sizeof(C) == 4) && (P <= 9);
+        bool general = true;
+        if constexpr (kLean) {
+            const bool lane_edge = per ? !contig : (padm != 0u || lvm != (1u << RW) - 1u);
+            general = __any_sync(FULL, lane_edge) || lastb || (!per && (ya - R * D < 0 || yb + R * D > n0i));
+        }
 
+        // level-0 row y (general loop: rows past the loaded region are
+        // prefetched for the ramp-down steps and never used, so skipped)
         auto load_row = [&](C(&v)[RW], int y) {
-            if (y >= hi0) return;  // below the region: never used
+            if (y >= hi0) return;
             if (per) {
-                // one wrap at most: the host keeps n0 >= 64 and n2 >= 128
+                // one wrap at most: the host keeps n0 >= 64 and n2 >= 136
                 const int yw = (y < 0) ? y + n0i : (y >= n0i ? y - n0i : y);
                 const T* rp = src + (int64_t)yw * lds;
                 if (contig) {
@@ -203,76 +220,160 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D))
                 for (int q = 0; q < RW; ++q) v[q] = ((lvm >> q) & 1u) ? Dt::load(rp + q) : C(0);
             }
         };
-
+        // One level's row, split in two parts of the canonical FMA chain:
+        // the head (every term whose row is older than the newest row of the
+        // level below) and the tail (the terms on that newest row, last in
+        // canonical order).  All levels' heads are independent of this
+        // step's other levels, so they are issued first, back to back; only
+        // the short tails form a chain through the levels.
+        // (star: the centre row's r edge cells come from the adjacent lanes)
+        constexpr int kTail = P - (EXT ? 2 * R + 1 : 1);  // first term on row +r
+        auto level_row = [&](int s, int cs, C(&acc)[4], const bool head) {
+            C e[EXT ? 1 : 4 + 2 * R];
+            if (!EXT && head) {
 #pragma unroll
-        for (int q = 0; q < PF; ++q) load_row(stage[q], lo0 + q);
+                for (int m = 0; m < 4; ++m) e[R + m] = ring[s - 1][cs][EXT ? 0 : m];
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    e[EXT ? 0 : i] = __shfl_up_sync(FULL, ring[s - 1][cs][4 - R + i], 1);
+                    e[EXT ? 0 : R + 4 + i] = __shfl_down_sync(FULL, ring[s - 1][cs][i], 1);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                if ((k < kTail) != head) continue;
+                const int dy = OFF.ds[k], dx = OFF.d2[k];
+                const int rs = (cs + dy + U) % U;
+                const C ck = coef(k);
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    C v;
+                    if constexpr (EXT) v = ring[s - 1][rs][X0 + m + dx];
+                    else v = (dy == 0) ? e[R + m + dx] : ring[s - 1][rs][m];
+                    acc[m] = (k == 0) ? Dt::mul(ck, v) : Dt::fma(ck, v, acc[m]);
+                }
+            }
+        };
+        // hand a level's row on: into its queue (box: with shuffled halo
+        // cells), or to global memory for the last level
+        auto put_row = [&](int s, int cs, int y, const C(&o)[4]) {
+            if (s < D) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) ring[s][cs][X0 + m] = o[m];
+                if constexpr (EXT) {
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        ring[s][cs][i] = __shfl_up_sync(FULL, o[4 - R + i], 1);
+                        ring[s][cs][X0 + 4 + i] = __shfl_down_sync(FULL, o[i], 1);
+                    }
+                }
+            } else {
+                const unsigned st = (y >= ya && y < yb) ? outm : 0u;
+                T* const rp = dst + (per ? (int64_t)y * lds : (int64_t)(y + pad) * lds + pad) + cb;
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    if ((st >> m) & 1u) rp[m] = Dt::narrow(o[m]);
+            }
+        };
 
         // ---- stream the strip ----------------------------------------------------
-        // The body is branch-free: every level computes a row at every step.
-        // A row outside its level's region (the ramp at the segment's ends,
-        // rows past the padded grid, the steps after the last) holds garbage
-        // that no kept value depends on: a row y of level s+1 inside its
-        // region reads rows y-r .. y+r of level s, all inside level s's
-        // region.  Only level-t rows inside the segment are stored.
-        for (int j0 = 0; j0 < niter; j0 += U) {
+        // Every level computes a row at every step.  A row outside its level's
+        // region (the ramp at the segment's ends, rows past the padded grid,
+        // the steps after the last) holds garbage that no kept value depends
+        // on: a row y of level s+1 inside its region reads rows y-r .. y+r of
+        // level s, all inside level s's region.  Only level-t rows inside the
+        // segment are stored.
+        if constexpr (kLean) {
+            // both copies from one template (this form measured fastest for
+            // the short stencils); rows past the region are clamped into it
+            auto load_row2 = [&](C(&v)[RW], int y, const bool G) {
+                y = min(y, hi0 - 1);
+                if (per) {
+                    const int yw = (y < 0) ? y + n0i : (y >= n0i ? y - n0i : y);
+                    const T* rp = src + (int64_t)yw * lds;
+                    if (!G || contig) {
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int yi = lo0 + j0 + u;  // level-0 row arriving now
-#pragma unroll
-                for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
-                load_row(stage[u % PF], yi + PF);
-#pragma unroll
-                for (int s = 1; s <= D; ++s) {
-                    const int y = yi - s * R;                   // row of level s computed now
-                    const int cs = ((u - s * R) % U + U) % U;   // queue slot of row y
-                    // pad rows and the levels past the last block's depth keep
-                    // the value below; pad columns likewise
-                    const bool copy = (s > deff) || (!per && (y < 0 || y >= n0i));
-                    const unsigned keep = copy ? 0xfu : padm;
-                    C e[4 + 2 * R];  // star: centre row with r cells of halo per side
-                    if constexpr (!EXT) {
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) e[R + m] = ring[s - 1][cs][m];
-#pragma unroll
-                        for (int i = 0; i < R; ++i) {
-                            e[i] = __shfl_up_sync(FULL, ring[s - 1][cs][4 - R + i], 1);
-                            e[R + 4 + i] = __shfl_down_sync(FULL, ring[s - 1][cs][i], 1);
-                        }
-                    }
-                    C acc[4];
-#pragma unroll
-                    for (int k = 0; k < P; ++k) {
-                        const int dy = OFF.ds[k], dx = OFF.d2[k];
-                        const int rs = (cs + dy + U) % U;
-                        const C ck = coef(k);
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) {
-                            C v;
-                            if constexpr (EXT) v = ring[s - 1][rs][X0 + m + dx];
-                            else v = (dy == 0) ? e[R + m + dx] : ring[s - 1][rs][m];
-                            acc[m] = (k == 0) ? Dt::mul(ck, v) : Dt::fma(ck, v, acc[m]);
-                        }
-                    }
-                    C o[4];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m] : Dt::widen(Dt::narrow(acc[m]));
-                    if (s < D) {
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) ring[s][cs][X0 + m] = o[m];
-                        if constexpr (EXT) {
-#pragma unroll
-                            for (int i = 0; i < R; ++i) {
-                                ring[s][cs][i] = __shfl_up_sync(FULL, o[4 - R + i], 1);
-                                ring[s][cs][X0 + 4 + i] = __shfl_down_sync(FULL, o[i], 1);
-                            }
-                        }
+                        for (int q = 0; q < RW; ++q) v[q] = Dt::load(rp + cw0 + q);
                     } else {
-                        const unsigned st = (y >= ya && y < yb) ? outm : 0u;
-                        T* const rp = dst + (per ? (int64_t)y * lds : (int64_t)(y + pad) * lds + pad) + cb;
+#pragma unroll
+                        for (int q = 0; q < RW; ++q) {
+                            const int c = cw0 + q;
+                            v[q] = Dt::load(rp + (c >= n2 ? c - n2 : c));
+                        }
+                    }
+                } else {
+                    const T* rp = src + (int64_t)(y + pad) * lds + (c0 + pad);
+#pragma unroll
+                    for (int q = 0; q < RW; ++q) v[q] = (!G || ((lvm >> q) & 1u)) ? Dt::load(rp + q) : C(0);
+                }
+            };
+            auto stream = [&](auto GEN) {
+                constexpr bool G = decltype(GEN)::value;
+#pragma unroll
+                for (int q = 0; q < PF; ++q) load_row2(stage[q], lo0 + q, G);
+                for (int j0 = 0; j0 < niter; j0 += U) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int yi = lo0 + j0 + u;  // level-0 row arriving now
+#pragma unroll
+                        for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
+                        load_row2(stage[u % PF], yi + PF, G);
+                        C acc[D][4];
+#pragma unroll
+                        for (int s = 1; s <= D; ++s) level_row(s, ((u - s * R) % U + U) % U, acc[s - 1], true);
+#pragma unroll
+                        for (int s = 1; s <= D; ++s) {
+                            const int y = yi - s * R;                  // row of level s computed now
+                            const int cs = ((u - s * R) % U + U) % U;  // queue slot of row y
+                            C o[4];
+                            level_row(s, cs, acc[s - 1], false);
+                            if constexpr (G) {
+                                const bool copy = (s > deff) || (!per && (y < 0 || y >= n0i));
+                                const unsigned keep = copy ? 0xfu : padm;
+#pragma unroll
+                                for (int m = 0; m < 4; ++m)
+                                    o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m]
+                                                              : Dt::widen(Dt::narrow(acc[s - 1][m]));
+                            } else {
+#pragma unroll
+                                for (int m = 0; m < 4; ++m) o[m] = Dt::widen(Dt::narrow(acc[s - 1][m]));
+                            }
+                            put_row(s, cs, y, o);
+                        }
+                    }
+                }
+            };
+            if (general)
+                stream(std::true_type{});
+            else
+                stream(std::false_type{});
+        } else {
+#pragma unroll
+            for (int q = 0; q < PF; ++q) load_row(stage[q], lo0 + q);
+            for (int j0 = 0; j0 < niter; j0 += U) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int yi = lo0 + j0 + u;  // level-0 row arriving now
+#pragma unroll
+                    for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
+                    load_row(stage[u % PF], yi + PF);
+                    C acc[D][4];
+#pragma unroll
+                    for (int s = 1; s <= D; ++s) level_row(s, ((u - s * R) % U + U) % U, acc[s - 1], true);
+#pragma unroll
+                    for (int s = 1; s <= D; ++s) {
+                        const int y = yi - s * R;                  // row of level s computed now
+                        const int cs = ((u - s * R) % U + U) % U;  // queue slot of row y
+                        // pad rows and the levels past the last block's depth
+                        // keep the value below; pad columns likewise
+                        const bool copy = (s > deff) || (!per && (y < 0 || y >= n0i));
+                        const unsigned keep = copy ? 0xfu : padm;
+                        C o[4];
+                        level_row(s, cs, acc[s - 1], false);
 #pragma unroll
                         for (int m = 0; m < 4; ++m)
-                            if ((st >> m) & 1u) rp[m] = Dt::narrow(o[m]);
+                            o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m] : Dt::widen(Dt::narrow(acc[s - 1][m]));
+                        put_row(s, cs, y, o);
                     }
                 }
             }
