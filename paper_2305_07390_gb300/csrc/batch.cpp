@@ -1,18 +1,23 @@
 // batch.cpp -- many independent problems in one persistent launch per kernel
 // type (ebisu_batch_*).
 //
-// Problems that share (ndim, shape, radius, dtype) form a group and run in one
-// launch of the temporally blocked kernel.  The group's work table lists
+// Problems that share (ndim, shape, radius, dtype) and kernel build form a
+// group and run in one launch of that temporally blocked kernel: the
+// register-streaming build (2D plans whose tuner chose it, grouped by depth)
+// or the shared-memory build (every other plan, with its shared-memory
+// parameters).  The group's work table lists
 // (problem, temporal block, tile) items in "waves": every tile of block 0 of
 // every problem, then block 1 of every problem, and so on, so that while one
 // problem's tiles of block b finish, the CTAs work on other problems instead
 // of waiting (the dependency counters of Section 4.3.2's one-wait-per-block
-// scheme are per problem).  Each problem keeps its own plan parameters (tile,
-// depth), so results are bit-identical to running it alone.
+// scheme are per problem, or per tile in the register-streaming build).
+// Each problem keeps its own plan parameters (tile, depth), so results are
+// bit-identical to running it alone.
 //
 // Workspace layout (all offsets 256-byte aligned):
 //   per group: Control block with one completion counter per problem
-//   GridDesc table (all problems), work tables (per group),
+//     (shared-memory build) or per tile of every member (register streaming)
+//   GridDesc table and RSGrid table (all problems), work tables (per group),
 //   one ping-pong grid buffer per problem.
 #include <algorithm>
 #include <cstring>
@@ -27,6 +32,7 @@ using namespace ebisu;
 struct BatchGroup {
     const ebisu_plan_s* kind = nullptr;  // representative plan (kernel type)
     int variant = 0;                     // kernel build (same for all members)
+    bool rs = false;                     // register-streaming build (variant = depth)
     std::vector<int> members;            // problem indices
     size_t ctl_off = 0, items_off = 0;
     int64_t nitems = 0;
@@ -40,13 +46,16 @@ struct ebisu_batch_s {
     std::vector<ebisu_plan_s> plans;
     std::vector<BatchGroup> groups;
     std::vector<GridDesc> descs;
+    std::vector<RSGrid> rsdescs;
+    std::vector<int32_t> tile_base;  // register streaming: first tile counter of a problem
+    std::vector<RSLayout> rsl;
     std::vector<std::vector<int32_t>> items;
     std::vector<const void*> in;
     std::vector<void*> out;
     std::vector<int64_t> steps;
     std::vector<size_t> grid_off;
     std::vector<bool> copy_in;
-    size_t desc_off = 0, total = 0;
+    size_t desc_off = 0, rsdesc_off = 0, total = 0;
     void* ws = nullptr;
     bool uploaded = false;
 };
@@ -54,13 +63,24 @@ struct ebisu_batch_s {
 namespace {
 
 struct Key {
-    int ndim, shape, radius, dtype, variant;
+    int ndim, shape, radius, dtype, rs, variant;
     bool operator<(const Key& o) const
     {
-        return std::tie(ndim, shape, radius, dtype, variant) <
-               std::tie(o.ndim, o.shape, o.radius, o.dtype, o.variant);
+        return std::tie(ndim, shape, radius, dtype, rs, variant) <
+               std::tie(o.ndim, o.shape, o.radius, o.dtype, o.rs, o.variant);
     }
 };
+
+// Does a plan run the register-streaming build (its tuner chose it)?
+bool uses_rs(const ebisu_plan_s* p)
+{
+    const ebisu_params& q = p->prm;
+    if (p->ndim != 2) return false;
+    if (!(q.variant == 2 || (q.variant == 1 && q.fused_variant == 2))) return false;
+    ebisu_params v = q;
+    v.variant = 2;
+    return rs_layout(p, v, nullptr) == EBISU_OK;
+}
 
 int64_t nblocks_of(const ebisu_plan_s* p, int64_t steps)
 {
@@ -71,6 +91,11 @@ int64_t nblocks_of(const ebisu_plan_s* p, int64_t steps)
 
 int64_t ntiles_of(const ebisu_plan_s* p)
 {
+    if (p->prm.variant == 2) {
+        RSLayout L;
+        rs_layout(p, p->prm, &L);
+        return (int64_t)L.nstrips * L.nsegs;
+    }
     GridDesc g;
     fill_grid_desc(p, nullptr, nullptr, nullptr, 1, false, &g);
     return g.ntiles;
@@ -82,29 +107,51 @@ int layout(ebisu_batch_s* b)
     const int n = b->n;
     std::map<Key, int> gid;
     for (int i = 0; i < n; ++i) {
-        // batches always run the fused kernel with the plan's tile and depth
-        // (a plan whose tuner preferred the one-step kernel keeps them too)
-        b->plans[i].prm = b->plans[i].tb_prm;
-        b->plans[i].prm.variant = 0;
+        // batches always run a fused kernel with the plan's tile and depth
+        // (a plan whose tuner preferred the one-step kernel keeps the best
+        // fused parameters too)
+        const bool rs = uses_rs(&b->plans[i]);
+        if (rs) {
+            b->plans[i].prm.variant = 2;
+        } else {
+            b->plans[i].prm = b->plans[i].tb_prm;
+            b->plans[i].prm.variant = 0;
+        }
         const ebisu_plan_s* p = &b->plans[i];
         if (b->steps[i] <= 0) continue;  // zero steps: plain copy, no kernel
-        Key k{p->ndim, p->shape, p->radius, p->dtype, kernel_variant(p->dtype, p->prm.ctas_per_sm)};
+        Key k{p->ndim, p->shape, p->radius, p->dtype, rs ? 1 : 0,
+              rs ? p->prm.depth : kernel_variant(p->dtype, p->prm.ctas_per_sm)};
         auto it = gid.find(k);
         if (it == gid.end()) {
             it = gid.emplace(k, (int)b->groups.size()).first;
             b->groups.emplace_back();
             b->groups.back().kind = p;
             b->groups.back().variant = k.variant;
+            b->groups.back().rs = rs;
         }
         b->groups[it->second].members.push_back(i);
     }
     size_t off = 0;
+    b->tile_base.assign(n, 0);
+    b->rsl.assign(n, RSLayout{});
     for (auto& g : b->groups) {
         g.ctl_off = off;
-        off += align_up(offsetof(Control, done) + sizeof(unsigned) * g.members.size(), kAlign);
+        size_t counters = g.members.size();
+        if (g.rs) {
+            counters = 0;
+            for (int m : g.members) {
+                rs_layout(&b->plans[m], b->plans[m].prm, &b->rsl[m]);
+                b->tile_base[m] = (int32_t)counters;
+                counters += (size_t)b->rsl[m].nstrips * b->rsl[m].nsegs;
+            }
+            if (counters >= (1u << 31)) return EBISU_ERR_UNSUPPORTED;
+        }
+        off += align_up(offsetof(Control, done) + sizeof(unsigned) * counters, kAlign);
     }
     b->desc_off = off;
     off += align_up(sizeof(GridDesc) * (size_t)std::max(n, 1), kAlign);
+    b->rsdesc_off = off;
+    off += align_up(sizeof(RSGrid) * (size_t)std::max(n, 1), kAlign);
     b->items.resize(b->groups.size());
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         BatchGroup& g = b->groups[gi];
@@ -125,6 +172,7 @@ int layout(ebisu_batch_s* b)
         g.nitems = (int64_t)it.size() / 3;
         g.items_off = off;
         off += align_up(sizeof(int32_t) * std::max<size_t>(it.size(), 1), kAlign);
+        if (g.rs) continue;  // no shared memory
         for (int m : g.members) {
             ebisu_params q = b->plans[m].prm;
             q.depth = (int)std::min<int64_t>(q.depth, b->steps[m]);
@@ -209,6 +257,7 @@ int ebisu_batch_create(int n, const ebisu_plan_t* plans, const void* const* in, 
     cudaStream_t st = (cudaStream_t)stream;
     char* ws = (char*)workspace;
     b->descs.assign(n, GridDesc{});
+    b->rsdescs.assign(n, RSGrid{});
     b->copy_in.assign(n, false);
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         const BatchGroup& g = b->groups[gi];
@@ -218,12 +267,19 @@ int ebisu_batch_create(int n, const ebisu_plan_t* plans, const void* const* in, 
             void* wsg = ws + b->grid_off[m];
             const int64_t nb = nblocks_of(p, b->steps[m]);
             b->copy_in[m] = (b->in[m] == b->out[m]) && (nb % 2 == 1);
-            fill_grid_desc(p, b->in[m], b->out[m], wsg, b->steps[m], b->copy_in[m], &b->descs[m]);
-            b->descs[m].grid_id = (int32_t)k;
+            if (g.rs) {
+                fill_rs_grid(p, b->rsl[m], b->in[m], b->out[m], wsg, b->steps[m], b->copy_in[m], &b->rsdescs[m]);
+                b->rsdescs[m].tile_base = b->tile_base[m];
+            } else {
+                fill_grid_desc(p, b->in[m], b->out[m], wsg, b->steps[m], b->copy_in[m], &b->descs[m]);
+                b->descs[m].grid_id = (int32_t)k;
+            }
         }
     }
     cudaError_t e = cudaMemcpyAsync(ws + b->desc_off, b->descs.data(), sizeof(GridDesc) * n,
                                     cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ws + b->rsdesc_off, b->rsdescs.data(), sizeof(RSGrid) * n, cudaMemcpyHostToDevice, st);
     for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
         const auto& it = b->items[gi];
         if (!it.empty())
@@ -235,7 +291,7 @@ int ebisu_batch_create(int n, const ebisu_plan_t* plans, const void* const* in, 
     for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
         BatchGroup& g = b->groups[gi];
         int occ = 0;
-        e = tb_occupancy(g.kind, g.variant, g.smem, &occ);
+        e = g.rs ? rs_occupancy(g.kind, g.variant, true, &occ) : tb_occupancy(g.kind, g.variant, g.smem, &occ);
         if (e != cudaSuccess) break;
         if (occ < 1) {
             delete b;
@@ -243,7 +299,9 @@ int ebisu_batch_create(int n, const ebisu_plan_t* plans, const void* const* in, 
         }
         int cps = 1;
         for (int m : g.members) cps = std::max(cps, b->plans[m].prm.ctas_per_sm);
-        g.grid = (int)std::min<int64_t>((int64_t)std::min(occ, cps) * device_info().sms, g.nitems);
+        const int64_t per_cta = g.rs ? kRSWarps : 1;  // work items one CTA takes at a time
+        g.grid = (int)std::min<int64_t>((int64_t)std::min(occ, cps) * device_info().sms,
+                                        (g.nitems + per_cta - 1) / per_cta);
     }
     if (e != cudaSuccess) {
         delete b;
@@ -277,6 +335,17 @@ int ebisu_batch_launch(ebisu_batch_t b, void* stream)
     for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
         const BatchGroup& g = b->groups[gi];
         if (g.nitems == 0) continue;
+        if (g.rs) {
+            RSParams prm;
+            memset(&prm, 0, sizeof(prm));
+            prm.grids = (const RSGrid*)(ws + b->rsdesc_off);
+            prm.items = (const int32_t*)(ws + g.items_off);
+            prm.nitems = g.nitems;
+            prm.ctl = (Control*)(ws + g.ctl_off);
+            prm.timeout_ns = wait_timeout_ns();
+            e = rs_launch(g.kind, g.variant, prm, g.grid, st);
+            continue;
+        }
         TBParams prm;
         memset(&prm, 0, sizeof(prm));
         prm.grids = (const GridDesc*)(ws + b->desc_off);

@@ -82,15 +82,24 @@ constexpr int rs_depth(int esize, int shape /*0 star, 1 box*/, int r, int which)
     return r == 1 ? (which ? 6 : 3) : (which ? 2 : 1);
 }
 
-struct RSParams {
+// Depth the register-streaming build defaults to (FP32/BF16 storage): the
+// faster of the two built depths on 8192^2 grids (measured on GB300).
+constexpr int rs_preferred_depth(int esize, int shape, int r)
+{
+    if (esize == 8) return 1;
+    if (shape == 0) return r == 1 ? (esize == 4 ? 8 : 4) : (r == 2 ? 3 : 2);
+    return r == 1 ? (esize == 4 ? 6 : 3) : 2;
+}
+
+// One problem of a register-streaming launch.
+struct RSGrid {
     const void* src0;   // input of the first temporal block
     void* out;          // final destination
     void* ws;           // ping-pong buffer
+    void* pad_dst0;     // buffers whose Dirichlet pad is filled from src0
+    void* pad_dst1;     //   during the first temporal block (or null)
     int64_t n0;         // interior rows
     int64_t lds;        // row pitch (elements)
-    int64_t nitems;     // nblocks * nstrips * nsegs
-    Control* ctl;
-    int64_t timeout_ns;
     int32_t n2;         // interior columns
     int32_t pad;        // Dirichlet pad (= radius), 0 if periodic
     int32_t periodic;
@@ -99,9 +108,20 @@ struct RSParams {
     int32_t nstrips, nsegs;
     int32_t nblocks;    // ceil(steps / depth)
     int32_t depth_last; // steps done by the last block (<= depth)
-    int32_t debug_stall;
+    int32_t tile_base;  // index of this problem's first tile counter
     double coef[kMaxPoints];
     float coef_f[kMaxPoints];  // the same rounded to FP32 (FP32/BF16 storage)
+};
+
+// Kernel parameters of a register-streaming launch.
+struct RSParams {
+    RSGrid g;                // the problem, when `grids` is null
+    const RSGrid* grids;     // batched: per-problem descriptors (device)
+    const int32_t* items;    // batched: (grid, block, tile) triples (device)
+    int64_t nitems;          // single: nblocks * nstrips * nsegs
+    Control* ctl;
+    int64_t timeout_ns;      // bound on every dependency wait
+    int32_t debug_stall;     // test hook: the first wait targets a count never reached
 };
 
 }  // namespace ebisu

@@ -279,17 +279,50 @@ cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int
     }
 }
 
-cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, int* blocks)
+cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, bool batch, int* blocks)
 {
     switch (p->dtype) {
-    case EBISU_F64: return rs_occupancy_f64(p->shape, p->radius, depth, blocks);
-    case EBISU_F32: return rs_occupancy_f32(p->shape, p->radius, depth, blocks);
-    default: return rs_occupancy_bf16(p->shape, p->radius, depth, blocks);
+    case EBISU_F64: return rs_occupancy_f64(p->shape, p->radius, depth, batch, blocks);
+    case EBISU_F32: return rs_occupancy_f32(p->shape, p->radius, depth, batch, blocks);
+    default: return rs_occupancy_bf16(p->shape, p->radius, depth, batch, blocks);
     }
 }
 
-// A run of the register-streaming build (the control block is already zeroed
-// and steps >= 1).
+int64_t fill_rs_grid(const ebisu_plan_s* p, const RSLayout& L, const void* in, void* out, void* wsgrid,
+                     int64_t steps, bool in_copied_to_ws, RSGrid* g)
+{
+    memset(g, 0, sizeof(*g));
+    const int D = p->prm.depth;
+    const int64_t nb = (steps + D - 1) / D;
+    g->src0 = in_copied_to_ws ? wsgrid : in;
+    g->out = out;
+    g->ws = wsgrid;
+    g->n0 = p->n[0];
+    g->lds = p->lds;
+    g->n2 = (int32_t)p->n[2];
+    g->pad = p->pad;
+    g->periodic = p->boundary == EBISU_PERIODIC;
+    g->S = L.S;
+    g->H = L.H;
+    g->nstrips = L.nstrips;
+    g->nsegs = L.nsegs;
+    g->nblocks = (int32_t)nb;
+    g->depth_last = (int32_t)(steps - (nb - 1) * D);
+    for (int k = 0; k < p->npts; ++k) {
+        g->coef[k] = p->coef[k];
+        g->coef_f[k] = (float)p->coef[k];
+    }
+    if (!g->periodic) {
+        // the kernel never writes pad cells: the buffers blocks write get the
+        // input's pad during the first block
+        void* d0 = ((nb - 1) % 2 == 0) ? out : wsgrid;
+        void* d1 = (nb >= 2) ? (((nb - 2) % 2 == 0) ? out : wsgrid) : nullptr;
+        if (d0 && d0 != g->src0 && d0 != in) g->pad_dst0 = d0;
+        if (d1 && d1 != g->src0 && d1 != in) g->pad_dst1 = d1;
+    }
+    return nb;
+}
+
 static int run_rs(ebisu_plan_t p, const void* in, void* out, int64_t steps, void* ws, cudaStream_t st,
                   int debug_stall)
 {
@@ -311,45 +344,15 @@ static int run_rs(ebisu_plan_t p, const void* in, void* out, int64_t steps, void
         e = cudaMemcpyAsync(wsgrid, in, bytes, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return fail_cuda(e);
     }
-    const void* src0 = copy_in ? wsgrid : in;
-    const bool per = p->boundary == EBISU_PERIODIC;
-    if (!per) {
-        // the kernel never writes pad cells: give the buffers it writes the input's pad
-        void* d0 = ((nb - 1) % 2 == 0) ? out : wsgrid;
-        void* d1 = (nb >= 2) ? (((nb - 2) % 2 == 0) ? out : wsgrid) : nullptr;
-        void* h0 = (d0 != src0 && d0 != in) ? d0 : nullptr;
-        void* h1 = (d1 && d1 != src0 && d1 != in) ? d1 : nullptr;
-        if (h0 || h1) {
-            e = pad_copy(p, src0, h0, h1, st);
-            if (e != cudaSuccess) return fail_cuda(e);
-        }
-    }
     RSParams prm;
     memset(&prm, 0, sizeof(prm));
-    prm.src0 = src0;
-    prm.out = out;
-    prm.ws = wsgrid;
-    prm.n0 = p->n[0];
-    prm.lds = p->lds;
+    fill_rs_grid(p, L, in, out, wsgrid, steps, copy_in, &prm.g);
     prm.nitems = nb * ntiles;
     prm.ctl = (Control*)ws;
     prm.timeout_ns = wait_timeout_ns();
-    prm.n2 = (int32_t)p->n[2];
-    prm.pad = p->pad;
-    prm.periodic = per ? 1 : 0;
-    prm.S = L.S;
-    prm.H = L.H;
-    prm.nstrips = L.nstrips;
-    prm.nsegs = L.nsegs;
-    prm.nblocks = (int32_t)nb;
-    prm.depth_last = (int32_t)(steps - (nb - 1) * D);
     prm.debug_stall = debug_stall;
-    for (int k = 0; k < p->npts; ++k) {
-        prm.coef[k] = p->coef[k];
-        prm.coef_f[k] = (float)p->coef[k];
-    }
     int occ = 0;
-    e = rs_occupancy(p, D, &occ);
+    e = rs_occupancy(p, D, false, &occ);
     if (e != cudaSuccess) return fail_cuda(e);
     if (occ < 1) return EBISU_ERR_UNSUPPORTED;
     int64_t grid = (int64_t)std::min(occ, q.ctas_per_sm) * dv.sms;
@@ -444,6 +447,27 @@ int ebisu_plan_create(int ndim, const int64_t* dims, int shape, int radius, cons
     }
     p->prm = best;
     p->tb_prm = best;
+    // 2D FP32/BF16: the register-streaming build is 2-5x faster than the
+    // shared-memory one at every measured stencil; default to it (the
+    // tuner still times both).  Segments of 128 rows (64 for BF16) give
+    // every resident warp several tiles on large grids.
+    if (p->ndim == 2 && p->dtype != EBISU_F64) {
+        ebisu_params v{};
+        v.variant = 2;
+        v.fused_variant = 2;
+        v.depth = rs_preferred_depth((int)p->esize, p->shape, p->radius);
+        v.tile_s = (int32_t)std::max<int64_t>((int64_t)v.depth * p->radius,
+                                              std::min<int64_t>(p->n[0], p->dtype == EBISU_BF16 ? 64 : 128));
+        v.ctas_per_sm = 8;
+        v.threads = kRSThreads;
+        RSLayout L;
+        if (rs_layout(p, v, &L) == EBISU_OK) {
+            v.tile_x = L.S;
+            v.tile_y = 1;
+            v.tile_s = L.H;
+            p->prm = v;
+        }
+    }
     *out = p;
     return EBISU_OK;
 }

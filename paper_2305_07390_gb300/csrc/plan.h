@@ -87,6 +87,11 @@ struct RSLayout {
 };
 int rs_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L);
 cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int grid, cudaStream_t st);
-cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, int* blocks);
+cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, bool batch, int* blocks);
+// Fill the descriptor of one register-streaming run of `steps` >= 1 steps
+// (src0: the first block's input; pads of the other written buffers are
+// filled by the kernel).  Returns the number of temporal blocks.
+int64_t fill_rs_grid(const ebisu_plan_s* p, const RSLayout& L, const void* in, void* out, void* wsgrid,
+                     int64_t steps, bool in_copied_to_ws, RSGrid* g);
 
 }  // namespace ebisu

@@ -50,20 +50,22 @@ struct RSGeom {
     // the star's widened centre row, the accumulators, and about 56 for
     // addresses, loop state and the item's geometry (the 25-point box keeps
     // more of its rows' values live across its 100 FMAs: found by compiling)
-    static constexpr int regs(int D)
+    static constexpr int P = Stencil<2, SHAPE, R>::P;
+    static constexpr int regs(int D, bool batch)
     {
-        return (D * U * RW + PF * RW + (EXT ? 0 : 4 + 2 * R) + 4) * WORDS + 56 + ((EXT && R == 2) ? 48 : 0);
+        return (D * U * RW + PF * RW + (EXT ? 0 : 4 + 2 * R) + 4 + (batch ? P : 0)) * WORDS + 56 +
+               ((EXT && R == 2) ? 48 : 0) + (batch ? 16 : 0);
     }
-    static constexpr int minb(int D)
+    static constexpr int minb(int D, bool batch)
     {
-        const int e = (regs(D) + 7) & ~7;
+        const int e = (regs(D, batch) + 7) & ~7;
         const int b = 65536 / (kRSThreads * e);
         return b < 1 ? 1 : (b > 8 ? 8 : b);
     }
 };
 
-template <class T, int SHAPE, int R, int D>
-__global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D))
+template <class T, int SHAPE, int R, int D, bool BATCH>
+__global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH))
     rs_kernel(const __grid_constant__ RSParams prm)
 {
     using G = RSGeom<T, SHAPE, R>;
@@ -83,31 +85,53 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D))
 
     const int lane = threadIdx.x & 31;
     Control* const ctl = prm.ctl;
-    const int64_t ntiles = (int64_t)prm.nstrips * prm.nsegs;
-    const bool per = prm.periodic != 0;
-    const int64_t n0 = prm.n0;
-    const int n2 = prm.n2;
-    const int pad = prm.pad;
-    const int64_t lds = prm.lds;
-    // coefficients stay in the parameter bank: FMAs take them as operands
+    // coefficients: in the parameter bank for a single problem (FMAs take
+    // them as operands), in registers (loaded per item) for a batch
+    C cr[BATCH ? P : 1];
     auto coef = [&](int k) -> C {
-        if constexpr (sizeof(C) == 8) return prm.coef[k];
-        else return prm.coef_f[k];
+        if constexpr (BATCH) return cr[k];
+        else if constexpr (sizeof(C) == 8) return prm.g.coef[k];
+        else return prm.g.coef_f[k];
     };
 
     C ring[D][U][RW];  // levels 0 .. D-1; level D goes to global memory
     C stage[PF][RW];   // level-0 rows in flight
 
     for (;;) {
-        // ---- pop an item: (temporal block, segment, strip) --------------------
+        // ---- pop an item: (problem, temporal block, tile) ---------------------
         long long it = -1;
+        int gi = 0, blk = 0, tile = 0;
         if (lane == 0 && *(volatile int*)&ctl->status == 0) it = (long long)atomicAdd(&ctl->next_item, 1u);
         it = __shfl_sync(FULL, it, 0);
         if (it < 0 || it >= prm.nitems) return;
-        const int blk = (int)(it / ntiles);
-        const int tile = (int)(it - (long long)blk * ntiles);
-        const int seg = tile / prm.nstrips;
-        const int strip = tile - seg * prm.nstrips;
+        if constexpr (BATCH) {
+            int v = 0;
+            if (lane < 3) v = prm.items[3 * it + lane];
+            gi = __shfl_sync(FULL, v, 0);
+            blk = __shfl_sync(FULL, v, 1);
+            tile = __shfl_sync(FULL, v, 2);
+        } else {
+            const long long ntiles = (long long)prm.g.nstrips * prm.g.nsegs;
+            blk = (int)(it / ntiles);
+            tile = (int)(it - (long long)blk * ntiles);
+        }
+        const RSGrid* const gd = BATCH ? prm.grids + gi : &prm.g;
+        const bool per = gd->periodic != 0;
+        const int64_t n0 = gd->n0;
+        const int n2 = gd->n2;
+        const int pad = gd->pad;
+        const int64_t lds = gd->lds;
+        const int S = gd->S, H = gd->H, nstrips = gd->nstrips, nsegs = gd->nsegs, nblocks = gd->nblocks;
+        unsigned* const done = &ctl->done[gd->tile_base];
+        if constexpr (BATCH) {
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                if constexpr (sizeof(C) == 8) cr[k] = gd->coef[k];
+                else cr[k] = gd->coef_f[k];
+            }
+        }
+        const int seg = tile / nstrips;
+        const int strip = tile - seg * nstrips;
 
         // ---- wait for the neighbouring tiles of the previous block -------------
         // lanes 0..8 each watch one of the 3 x 3 neighbours (bounded waits)
@@ -116,14 +140,14 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D))
             int sg = seg + lane / 3 - 1, sx = strip + lane % 3 - 1;
             bool exists = true;
             if (per) {
-                sg = (sg + prm.nsegs) % prm.nsegs;
-                sx = (sx + prm.nstrips) % prm.nstrips;
+                sg = (sg + nsegs) % nsegs;
+                sx = (sx + nstrips) % nstrips;
             } else {
-                exists = sg >= 0 && sg < prm.nsegs && sx >= 0 && sx < prm.nstrips;
+                exists = sg >= 0 && sg < nsegs && sx >= 0 && sx < nstrips;
             }
             if (exists) {
                 const unsigned target = (unsigned)blk + (prm.debug_stall ? 1u : 0u);
-                const unsigned* cnt = &ctl->done[(int64_t)sg * prm.nstrips + sx];
+                const unsigned* cnt = &done[(int64_t)sg * nstrips + sx];
                 if (ld_acquire_u32(cnt) < target) {
                     const uint64_t t0 = global_ns();
                     unsigned ns = 32;
@@ -144,24 +168,54 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D))
         if (!__all_sync(FULL, ok)) return;
 
         // ---- geometry ------------------------------------------------------------
-        const bool lastb = (blk == prm.nblocks - 1);
-        const int deff = lastb ? prm.depth_last : D;  // levels above deff pass values through
-        const bool dst_is_out = ((prm.nblocks - 1 - blk) & 1) == 0;
-        T* const dst = reinterpret_cast<T*>(dst_is_out ? prm.out : prm.ws);
-        const T* const src = (blk == 0) ? reinterpret_cast<const T*>(prm.src0)
-                                        : reinterpret_cast<const T*>(dst_is_out ? prm.ws : prm.out);
-        const int xs = strip * prm.S;          // first output column of the strip
-        const int xe = min(xs + prm.S, n2);    // end of the output columns
+        const bool lastb = (blk == nblocks - 1);
+        const int deff = lastb ? gd->depth_last : D;  // levels above deff pass values through
+        const bool dst_is_out = ((nblocks - 1 - blk) & 1) == 0;
+        T* const dst = reinterpret_cast<T*>(dst_is_out ? gd->out : gd->ws);
+        const T* const src = (blk == 0) ? reinterpret_cast<const T*>(gd->src0)
+                                        : reinterpret_cast<const T*>(dst_is_out ? gd->ws : gd->out);
+        const int xs = strip * S;              // first output column of the strip
+        const int xe = min(xs + S, n2);        // end of the output columns
         const int cb = xs - D * R + 4 * lane;  // column of this lane's cell 0
         // rows (int: the host keeps n0 + 2 * pad below 2^31)
-        const int ya = seg * prm.H;
-        const int yb = min(ya + prm.H, (int)n0);
+        const int ya = seg * H;
+        const int yb = min(ya + H, (int)n0);
         const int n0i = (int)n0;
         // rows of level s: [ya - r(D-s), yb + r(D-s)), clipped to the padded
         // grid; level 0 is loaded over [lo0, hi0)
         const int lo0 = per ? ya - R * D : max(ya - R * D, -pad);
         const int hi0 = per ? yb + R * D : min(yb + R * D, n0i + pad);
         const int niter = yb + D * R - lo0;  // level D's last row arrives last
+
+        // ---- first temporal block: give the buffers later blocks write the
+        // input's Dirichlet pad (this tile's share: the pad cells next to its
+        // output region).  A tile of block 1 that reads such a cell reaches
+        // at most t*r cells past its own output, so the writer is one of the
+        // 3 x 3 neighbours it waits for.
+        if (blk == 0 && !per && (gd->pad_dst0 || gd->pad_dst1)) {
+            const bool fs = strip == 0, ls = strip == nstrips - 1, fg = seg == 0, lg = seg == nsegs - 1;
+            if (fs || ls || fg || lg) {
+                const T* const s0 = reinterpret_cast<const T*>(gd->src0);
+                T* const h0 = reinterpret_cast<T*>(gd->pad_dst0);
+                T* const h1 = reinterpret_cast<T*>(gd->pad_dst1);
+                const int x0 = fs ? -pad : xs, x1 = ls ? n2 + pad : xe;
+                const int y0 = fg ? -pad : ya, y1 = lg ? (int)n0 + pad : yb;
+                auto copy_cell = [&](int y, int c) {
+                    const int64_t g = (int64_t)(y + pad) * lds + (c + pad);
+                    const T v = Dt::raw(s0 + g);
+                    if (h0) h0[g] = v;
+                    if (h1) h1[g] = v;
+                };
+                for (int y = y0; y < y1; ++y) {
+                    if (y < 0 || y >= (int)n0) {  // a pad row: all of the tile's columns
+                        for (int c = x0 + lane; c < x1; c += 32) copy_cell(y, c);
+                    } else {                      // an interior row: its pad columns
+                        if (fs && lane < pad) copy_cell(y, -pad + lane);
+                        if (ls && lane < pad) copy_cell(y, n2 + lane);
+                    }
+                }
+            }
+        }
 
         // loaded columns cb - X0 .. cb - X0 + RW - 1: which exist (Dirichlet:
         // inside the padded row), and whether they are one contiguous run
@@ -382,7 +436,7 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D))
         // ---- publish completion of this tile -------------------------------------
         __threadfence();
         __syncwarp();
-        if (lane == 0) red_release_add_u32(&ctl->done[tile], 1u);
+        if (lane == 0) red_release_add_u32(&done[tile], 1u);
     }
 }
 

@@ -307,7 +307,7 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
             const int D = rs_depth((int)plan->esize, plan->shape, plan->radius, which);
             if (which == 1 && D == rs_depth((int)plan->esize, plan->shape, plan->radius, 0)) break;
             int occ = 0;
-            if (rs_occupancy(plan, D, &occ) != cudaSuccess || occ < 1) {
+            if (rs_occupancy(plan, D, false, &occ) != cudaSuccess || occ < 1) {
                 cudaGetLastError();
                 continue;
             }

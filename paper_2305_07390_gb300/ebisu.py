@@ -252,6 +252,11 @@ class Plan:
         return p
 
     def set_params(self, **kw):
+        """Update the given fields of the plan's parameters.  Explicit tile
+        extents (tile_x / tile_y) describe the shared-memory build, so unless
+        `variant` is given too they select it (variant 0)."""
+        if "variant" not in kw and ("tile_x" in kw or "tile_y" in kw):
+            kw = dict(kw, variant=0)
         p = self.params()
         for k, v in kw.items():
             setattr(p, k, int(v))

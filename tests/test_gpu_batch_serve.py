@@ -54,6 +54,81 @@ def mixed_problems(eb, count, seed):
     return probs
 
 
+def mixed_rs_problems(eb, count, seed):
+    """Mixed problems, most of them set to the register-streaming build
+    (every dtype, both built depths, star and box), the rest to the
+    shared-memory build; steps often leave a partial last block."""
+    rng = np.random.default_rng(seed)
+    probs = []
+    for i in range(count):
+        dtype = int(rng.integers(0, 3))
+        shape, r = [(0, 1), (1, 1), (0, 2), (1, 2), (0, 3)][i % 5]
+        ny, nx = int(rng.integers(64, 300)), int(rng.integers(140, 600))
+        steps = int(rng.integers(1, 25))
+        bd = int(i % 4 == 3)
+        plan, x, held, c_held = make_problem(eb, 2, (ny, nx), shape, r, dtype, bd, seed * 100 + i)
+        if i % 3 != 2:
+            d = plan.rs_depths()[i % 2]
+            try:
+                plan.set_params(variant=2, depth=d, tile_s=int(rng.integers(d * r, 90)), ctas_per_sm=4)
+            except eb.EbisuError:
+                plan.set_params(tile_x=128, tile_s=40, depth=2, variant=0)
+        else:
+            plan.set_params(tile_x=128, tile_s=40, depth=2, variant=0)
+        probs.append((plan, x, held, c_held, steps))
+    return probs
+
+
+def test_batch_register_streaming_equals_alone_and_oracle():
+    eb = _eb()
+    probs = mixed_rs_problems(eb, 16, 11)
+    assert sum(p[0].params().variant == 2 for p in probs) >= 8
+    plans = [p[0] for p in probs]
+    xs = [p[1] for p in probs]
+    steps = [p[4] for p in probs]
+    ys = [torch.empty_like(x) for x in xs]
+    ws = torch.empty(eb.batch_workspace_bytes(plans, steps), dtype=torch.uint8, device="cuda")
+    eb.batch_run(plans, xs, ys, steps, ws)
+    torch.cuda.synchronize()
+    for (plan, x, held, c_held, st), y in zip(probs, ys):
+        assert torch.equal(y, alone(plan, x, st)), "batched result differs from the problem alone"
+        ref = oracle.run(held, plan.shape, plan.radius, c_held, plan.boundary, st)
+        assert oracle.rel_linf(y.double().cpu().numpy(), ref, plan.pad) <= TOL[plan.dtype]
+
+
+def test_batch_register_streaming_graph_replay_and_serve():
+    eb = _eb()
+    probs = mixed_rs_problems(eb, 8, 12)
+    plans = [p[0] for p in probs]
+    xs = [p[1] for p in probs]
+    steps = [p[4] for p in probs]
+    ys = [torch.empty_like(x) for x in xs]
+    ws = torch.empty(eb.batch_workspace_bytes(plans, steps), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b = eb.Batch(plans, xs, ys, steps, ws)
+        b.launch()
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            b.launch()
+    for y in ys:
+        y.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert b.sync() == 0
+    for (plan, x, _, _, st), y in zip(probs, ys):
+        assert torch.equal(y, alone(plan, x, st))
+    srv = eb.Server(hbm_budget=2 << 30, max_slots=3)
+    ys2 = [torch.empty_like(x) for x in xs]
+    tickets = [srv.submit(p[0], p[1], y, p[4]) for p, y in zip(probs, ys2)]
+    for t in tickets:
+        srv.wait(t)
+    for y, y2 in zip(ys, ys2):
+        assert torch.equal(y, y2), "served result differs from the problem alone"
+    srv.close()
+
+
 def test_batch_equals_alone_and_oracle():
     eb = _eb()
     probs = mixed_problems(eb, 14, 3)
