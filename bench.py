@@ -629,9 +629,7 @@ def main():
         "precision_forms": forms,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": max(e2e_ms)},
-        # per solve: the blocked kernel, plus the pad copy the register-
-        # streaming build launches before it (Dirichlet)
-        "gpu_launches": args.steps * sum(1 + (p["plan"].params().variant == 2) for p in probs),
+        "gpu_launches": len(probs) * args.steps,  # one persistent launch per solve
         "clocks": clk,
     }
     if cpu is not None:
