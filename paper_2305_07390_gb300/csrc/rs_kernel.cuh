@@ -44,7 +44,14 @@ struct RSGeom {
     static constexpr int U = 2 * R + 1;                       // rows queued per level
     static constexpr bool EXT = (SHAPE == kBox);              // rows stored with halo
     static constexpr int RW = EXT ? 4 + 2 * R : 4;            // values per queued row
-    static constexpr int PF = (sizeof(C) == 8) ? 1 : U;       // level-0 rows in flight (divides U)
+    // Level-0 rows in flight.  FP32/FP64 storage: PFS rows staged in shared
+    // memory by cp.async (each lane copies and later reads back only its own
+    // columns, so no barrier is needed).  BF16 (2-byte elements, below
+    // cp.async's 4-byte minimum) and the 25-point box (measured faster
+    // with its 5 rows in registers): PF rows in registers (PF divides U).
+    static constexpr bool ASYNC = sizeof(T) >= 4 && !(EXT && R == 2);
+    static constexpr int PFS = (sizeof(T) == 8) ? 4 : 8;
+    static constexpr int PF = ASYNC ? 1 : ((sizeof(C) == 8) ? 1 : U);
     static constexpr int WORDS = (int)sizeof(C) / 4;
     // registers a thread needs at depth D: the queues, the rows in flight,
     // the star's widened centre row, the accumulators, and about 56 for
@@ -53,7 +60,7 @@ struct RSGeom {
     static constexpr int P = Stencil<2, SHAPE, R>::P;
     static constexpr int regs(int D, bool batch)
     {
-        return (D * U * RW + PF * RW + (EXT ? 0 : 4 + 2 * R) + 4 + (batch ? P : 0)) * WORDS + 56 +
+        return (D * U * RW + (ASYNC ? 0 : PF * RW) + (EXT ? 0 : 4 + 2 * R) + 4 + (batch ? P : 0)) * WORDS + 56 +
                ((EXT && R == 2) ? 48 : 0) + (batch ? 16 : 0);
     }
     static constexpr int minb(int D, bool batch)
@@ -63,6 +70,18 @@ struct RSGeom {
         return b < 1 ? 1 : (b > 8 ? 8 : b);
     }
 };
+
+// cp.async of one 4- or 8-byte element; src_size 0 writes zeros and reads nothing.
+template <int BYTES>
+__device__ __forceinline__ void rs_cp_async(void* smem, const void* gmem, int src_size)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(sa), "l"(gmem), "n"(BYTES), "r"(src_size)
+                 : "memory");
+}
+__device__ __forceinline__ void rs_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void rs_cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 template <class T, int SHAPE, int R, int D, bool BATCH>
 __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH))
@@ -94,8 +113,13 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
         else return prm.g.coef_f[k];
     };
 
-    C ring[D][U][RW];  // levels 0 .. D-1; level D goes to global memory
-    C stage[PF][RW];   // level-0 rows in flight
+    constexpr bool ASYNC = G::ASYNC;
+    constexpr int PFS = G::PFS;
+    C ring[D][U][RW];                 // levels 0 .. D-1; level D goes to global memory
+    C stage[ASYNC ? 1 : PF][RW];      // level-0 rows in flight (registers)
+    // level-0 rows in flight (shared memory): [warp][slot][lane][column]
+    __shared__ __align__(16) T s_stage[ASYNC ? kRSWarps * PFS * 32 * RW : 1];
+    T* const my_stage = s_stage + (ASYNC ? ((threadIdx.x >> 5) * PFS * 32 + lane) * RW : 0);
 
     for (;;) {
         // ---- pop an item: (problem, temporal block, tile) ---------------------
@@ -274,6 +298,43 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                 for (int q = 0; q < RW; ++q) v[q] = ((lvm >> q) & 1u) ? Dt::load(rp + q) : C(0);
             }
         };
+        // Shared-memory staging (FP32/FP64): row y's columns go to this
+        // lane's slot by cp.async (zero-filled where the column does not
+        // exist); rows past the loaded region are skipped (general loop) or
+        // clamped into it (lean loop).  One commit group per row, always.
+        auto issue_row = [&](int slot, int y, const bool G, const bool lean) {
+            T* const sp = my_stage + slot * (32 * RW);
+            bool skip = false;
+            if (lean) y = min(y, hi0 - 1);
+            else skip = (y >= hi0);
+            if (!skip) {
+                if (per) {
+                    const int yw = (y < 0) ? y + n0i : (y >= n0i ? y - n0i : y);
+                    const T* rp = src + (int64_t)yw * lds;
+#pragma unroll
+                    for (int q = 0; q < RW; ++q) {
+                        const int c = cw0 + q;
+                        rs_cp_async<sizeof(T)>(sp + q, rp + ((!G || contig) ? c : (c >= n2 ? c - n2 : c)), sizeof(T));
+                    }
+                } else {
+                    const T* rp = src + (int64_t)(y + pad) * lds + (c0 + pad);
+#pragma unroll
+                    for (int q = 0; q < RW; ++q) {
+                        const bool ok = !G || ((lvm >> q) & 1u);
+                        rs_cp_async<sizeof(T)>(sp + q, ok ? rp + q : src, ok ? (int)sizeof(T) : 0);
+                    }
+                }
+            }
+            rs_cp_commit();
+        };
+        // the oldest row in flight into level 0's queue slot u
+        auto take_row = [&](int u, int slot) {
+            rs_cp_wait<PFS - 1>();
+            const T* const sp = my_stage + slot * (32 * RW);
+#pragma unroll
+            for (int q = 0; q < RW; ++q) ring[0][u][q] = Dt::widen(sp[q]);
+        };
+
         // One level's row, split in two parts of the canonical FMA chain:
         // the head (every term whose row is older than the newest row of the
         // level below) and the tail (the terms on that newest row, last in
@@ -363,15 +424,26 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
             };
             auto stream = [&](auto GEN) {
                 constexpr bool G = decltype(GEN)::value;
+                if constexpr (ASYNC) {
 #pragma unroll
-                for (int q = 0; q < PF; ++q) load_row2(stage[q], lo0 + q, G);
+                    for (int q = 0; q < PFS; ++q) issue_row(q, lo0 + q, G, true);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < PF; ++q) load_row2(stage[q], lo0 + q, G);
+                }
                 for (int j0 = 0; j0 < niter; j0 += U) {
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         const int yi = lo0 + j0 + u;  // level-0 row arriving now
+                        if constexpr (ASYNC) {
+                            const int slot = (j0 + u) & (PFS - 1);
+                            take_row(u, slot);
+                            issue_row(slot, yi + PFS, G, true);
+                        } else {
 #pragma unroll
-                        for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
-                        load_row2(stage[u % PF], yi + PF, G);
+                            for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
+                            load_row2(stage[u % PF], yi + PF, G);
+                        }
                         C acc[D][4];
 #pragma unroll
                         for (int s = 1; s <= D; ++s) level_row(s, ((u - s * R) % U + U) % U, acc[s - 1], true);
@@ -402,15 +474,26 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
             else
                 stream(std::false_type{});
         } else {
+            if constexpr (ASYNC) {
 #pragma unroll
-            for (int q = 0; q < PF; ++q) load_row(stage[q], lo0 + q);
+                for (int q = 0; q < PFS; ++q) issue_row(q, lo0 + q, true, false);
+            } else {
+#pragma unroll
+                for (int q = 0; q < PF; ++q) load_row(stage[q], lo0 + q);
+            }
             for (int j0 = 0; j0 < niter; j0 += U) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int yi = lo0 + j0 + u;  // level-0 row arriving now
+                    if constexpr (ASYNC) {
+                        const int slot = (j0 + u) & (PFS - 1);
+                        take_row(u, slot);
+                        issue_row(slot, yi + PFS, true, false);
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
-                    load_row(stage[u % PF], yi + PF);
+                        for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
+                        load_row(stage[u % PF], yi + PF);
+                    }
                     C acc[D][4];
 #pragma unroll
                     for (int s = 1; s <= D; ++s) level_row(s, ((u - s * R) % U + U) % U, acc[s - 1], true);
@@ -432,6 +515,8 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                 }
             }
         }
+
+        if constexpr (ASYNC) rs_cp_wait<0>();  // the slots are reused by the next item
 
         // ---- publish completion of this tile -------------------------------------
         __threadfence();
