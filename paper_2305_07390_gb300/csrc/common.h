@@ -82,6 +82,15 @@ constexpr int rs_depth(int esize, int shape /*0 star, 1 box*/, int r, int which)
     return r == 1 ? (which ? 6 : 3) : (which ? 2 : 1);
 }
 
+// 3D register-streaming build (depth 1, FP64): which stencils it covers and
+// the rows of a warp's patch.
+constexpr bool rs3_built(int esize, int shape, int r)
+{
+    return esize == 8 && (r == 1 || (shape == 0 && r == 2));
+}
+constexpr int rs3_rows(int r) { return r <= 2 ? 2 : 1; }
+constexpr int kRS3Cols = 64;  // columns a warp holds (32 lanes x 2)
+
 // Depth the register-streaming build defaults to (FP32/BF16 storage): the
 // faster of the two built depths on 8192^2 grids (measured on GB300).
 constexpr int rs_preferred_depth(int esize, int shape, int r)
@@ -122,6 +131,27 @@ struct RSParams {
     Control* ctl;
     int64_t timeout_ns;      // bound on every dependency wait
     int32_t debug_stall;     // test hook: the first wait targets a count never reached
+};
+
+// Kernel parameters of a 3D register-streaming launch (depth 1).
+struct RS3Params {
+    const void* src0;    // input of the first step
+    void* out;           // final destination
+    void* ws;            // ping-pong buffer
+    int64_t n[3];        // interior extents (z, y, x)
+    int64_t lds, ld1;    // element strides of z and y
+    int64_t nitems;      // nblocks * nstrips * nbands * nsegs
+    Control* ctl;
+    int64_t timeout_ns;
+    int32_t pad;         // Dirichlet pad (= radius), 0 if periodic
+    int32_t periodic;
+    int32_t S;           // output columns per strip (64 - 2 * radius)
+    int32_t H;           // output planes per z segment
+    int32_t nstrips, nbands, nsegs;
+    int32_t nblocks;     // = steps (depth 1)
+    int32_t debug_stall;
+    double coef[kMaxPoints];
+    float coef_f[kMaxPoints];
 };
 
 }  // namespace ebisu

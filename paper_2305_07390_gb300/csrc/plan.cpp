@@ -102,8 +102,41 @@ size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q)
     return slots * (size_t)plane_capacity(p, q) * p->esize;
 }
 
+// 3D register-streaming build: 64-column strips (S = 64 - 2r), bands of TY
+// rows, z segments of H planes; depth 1 only.
+static int rs3_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L)
+{
+    const int r = p->radius;
+    if (!rs3_built((int)p->esize, p->shape, r) || q.depth != 1) return EBISU_ERR_UNSUPPORTED;
+    const int64_t n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
+    if (n0 + 2 * p->pad > (1LL << 30) || n1 + 2 * p->pad > (1LL << 30) || n2 + 2 * p->pad > (1LL << 30))
+        return EBISU_ERR_UNSUPPORTED;
+    const bool per = p->boundary == EBISU_PERIODIC;
+    // the kernel wraps a periodic index at most once
+    if (per && (n0 < 16 || n1 < 16 || n2 < 72)) return EBISU_ERR_UNSUPPORTED;
+    const int S = kRS3Cols - 2 * r, TY = rs3_rows(r);
+    const int64_t H = (q.tile_s <= 0) ? n0 : std::min<int64_t>(q.tile_s, n0);
+    const int64_t ns = (n2 + S - 1) / S, nb = (n1 + TY - 1) / TY, ng = (n0 + H - 1) / H;
+    // a tile's inputs reach r cells into its neighbours and no further
+    if ((ng > 1 && H < r) || TY < r) return EBISU_ERR_UNSUPPORTED;
+    if (per && ((ns > 1 && n2 - (ns - 1) * S < r) || (nb > 1 && n1 - (nb - 1) * TY < r) ||
+                (ng > 1 && n0 - (ng - 1) * H < r)))
+        return EBISU_ERR_UNSUPPORTED;
+    if (ns * nb * ng > kRSMaxTiles) return EBISU_ERR_UNSUPPORTED;
+    if (L) {
+        L->S = S;
+        L->H = (int)H;
+        L->nstrips = (int)ns;
+        L->nsegs = (int)ng;
+        L->TY = TY;
+        L->nbands = (int)nb;
+    }
+    return EBISU_OK;
+}
+
 int rs_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L)
 {
+    if (p->ndim == 3) return rs3_layout(p, q, L);
     if (p->ndim != 2) return EBISU_ERR_UNSUPPORTED;
     const int r = p->radius, es = (int)p->esize;
     if (q.depth != rs_depth(es, p->shape, r, 0) && q.depth != rs_depth(es, p->shape, r, 1))
@@ -279,6 +312,18 @@ cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int
     }
 }
 
+cudaError_t rs3_launch(const ebisu_plan_s* p, const RS3Params& prm, int grid, cudaStream_t st)
+{
+    if (p->dtype != EBISU_F64) return cudaErrorInvalidValue;
+    return rs3_launch_f64(p->shape, p->radius, prm, grid, st);
+}
+
+cudaError_t rs3_occupancy(const ebisu_plan_s* p, int* blocks)
+{
+    if (p->dtype != EBISU_F64) return cudaErrorInvalidValue;
+    return rs3_occupancy_f64(p->shape, p->radius, blocks);
+}
+
 cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, bool batch, int* blocks)
 {
     switch (p->dtype) {
@@ -323,9 +368,79 @@ int64_t fill_rs_grid(const ebisu_plan_s* p, const RSLayout& L, const void* in, v
     return nb;
 }
 
+// A run of the 3D register-streaming build (depth 1: one temporal block per
+// step).  The kernel never writes pad cells: the buffers it writes first get
+// the input's pad from a copy kernel.
+static int run_rs3(ebisu_plan_t p, const void* in, void* out, int64_t steps, void* ws, cudaStream_t st,
+                   int debug_stall)
+{
+    const ebisu_params& q = p->prm;
+    RSLayout L;
+    int rc = rs_layout(p, q, &L);
+    if (rc != EBISU_OK) return rc;
+    const int64_t nb = steps;
+    const int64_t ntiles = (int64_t)L.nstrips * L.nbands * L.nsegs;
+    const DeviceInfo& dv = device_info();
+    if (nb * ntiles + 64LL * 16 * dv.sms * kRSWarps >= (1LL << 32)) return EBISU_ERR_UNSUPPORTED;
+    const size_t bytes = (size_t)p->elems * p->esize;
+    void* wsgrid = (char*)ws + kControlBytes;
+    cudaError_t e = cudaSuccess;
+    const bool copy_in = (in == out) && (nb % 2 == 1);
+    if (copy_in) {
+        e = cudaMemcpyAsync(wsgrid, in, bytes, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return fail_cuda(e);
+    }
+    const void* src0 = copy_in ? wsgrid : in;
+    const bool per = p->boundary == EBISU_PERIODIC;
+    if (!per) {
+        void* d0 = ((nb - 1) % 2 == 0) ? out : wsgrid;
+        void* d1 = (nb >= 2) ? (((nb - 2) % 2 == 0) ? out : wsgrid) : nullptr;
+        void* h0 = (d0 != src0 && d0 != in) ? d0 : nullptr;
+        void* h1 = (d1 && d1 != src0 && d1 != in) ? d1 : nullptr;
+        if (h0 || h1) {
+            e = pad_copy(p, src0, h0, h1, st);
+            if (e != cudaSuccess) return fail_cuda(e);
+        }
+    }
+    RS3Params prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.src0 = src0;
+    prm.out = out;
+    prm.ws = wsgrid;
+    for (int i = 0; i < 3; ++i) prm.n[i] = p->n[i];
+    prm.lds = p->lds;
+    prm.ld1 = p->ld1;
+    prm.nitems = nb * ntiles;
+    prm.ctl = (Control*)ws;
+    prm.timeout_ns = wait_timeout_ns();
+    prm.pad = p->pad;
+    prm.periodic = per ? 1 : 0;
+    prm.S = L.S;
+    prm.H = L.H;
+    prm.nstrips = L.nstrips;
+    prm.nbands = L.nbands;
+    prm.nsegs = L.nsegs;
+    prm.nblocks = (int32_t)nb;
+    prm.debug_stall = debug_stall;
+    for (int k = 0; k < p->npts; ++k) {
+        prm.coef[k] = p->coef[k];
+        prm.coef_f[k] = (float)p->coef[k];
+    }
+    int occ = 0;
+    e = rs3_occupancy(p, &occ);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (occ < 1) return EBISU_ERR_UNSUPPORTED;
+    int64_t grid = (int64_t)std::min(occ, q.ctas_per_sm) * dv.sms;
+    grid = std::min<int64_t>(grid, (prm.nitems + kRSWarps - 1) / kRSWarps);
+    e = rs3_launch(p, prm, (int)grid, st);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return EBISU_OK;
+}
+
 static int run_rs(ebisu_plan_t p, const void* in, void* out, int64_t steps, void* ws, cudaStream_t st,
                   int debug_stall)
 {
+    if (p->ndim == 3) return run_rs3(p, in, out, steps, ws, st, debug_stall);
     const ebisu_params& q = p->prm;
     RSLayout L;
     int rc = rs_layout(p, q, &L);
@@ -513,8 +628,8 @@ int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* q)
     if (v.variant == 2) {
         RSLayout L;
         rs_layout(plan, v, &L);
-        v.tile_x = L.S;  // derived: 128 - 2 * depth * radius
-        v.tile_y = 1;
+        v.tile_x = L.S;  // derived: 128 - 2 * depth * radius (3D: 64 - 2 * radius)
+        v.tile_y = L.TY;
         v.tile_s = L.H;
         v.fused_variant = 2;
     } else if (build == 0) {
@@ -531,7 +646,7 @@ int ebisu_plan_rs_depths(ebisu_plan_t plan, int* shallow, int* deep)
 {
     if (!plan || !shallow || !deep) return EBISU_ERR_INVALID_ARG;
     if (plan->ndim != 2) {
-        *shallow = *deep = 0;
+        *shallow = *deep = rs3_built((int)plan->esize, plan->shape, plan->radius) ? 1 : 0;
         return EBISU_OK;
     }
     *shallow = rs_depth((int)plan->esize, plan->shape, plan->radius, 0);

@@ -84,10 +84,13 @@ int64_t wait_timeout_ns();
 // Register-streaming build (variant 2, 2D): strips of S columns, segments of H rows.
 struct RSLayout {
     int S, H, nstrips, nsegs;
+    int TY = 1, nbands = 1;  // 3D: rows per patch, patches along y
 };
 int rs_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L);
 cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int grid, cudaStream_t st);
 cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, bool batch, int* blocks);
+cudaError_t rs3_launch(const ebisu_plan_s* p, const RS3Params& prm, int grid, cudaStream_t st);
+cudaError_t rs3_occupancy(const ebisu_plan_s* p, int* blocks);
 // Fill the descriptor of one register-streaming run of `steps` >= 1 steps
 // (src0: the first block's input; pads of the other written buffers are
 // filled by the kernel).  Returns the number of temporal blocks.

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "dispatch.h"
+#include "rs3_kernel.cuh"
 #include "rs_kernel.cuh"
 
 namespace ebisu {
@@ -45,6 +46,36 @@ static cudaError_t rs_occupancy_t(int shape, int r, int depth, bool batch, int* 
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kRSThreads, 0);
 }
 
+// 3D (depth 1): the 7- and 13-point stars and the 27-point box, FP64 only
+// (FP32/BF16 3D grids gain from deeper blocks: the shared-memory kernel).
+template <class T>
+static const void* rs3_kernel_ptr(int shape, int r)
+{
+    if constexpr (sizeof(T) == 8) {
+        if (shape == kStar && r == 1) return (const void*)&rs3_kernel<T, kStar, 1>;
+        if (shape == kStar && r == 2) return (const void*)&rs3_kernel<T, kStar, 2>;
+        if (shape == kBox && r == 1) return (const void*)&rs3_kernel<T, kBox, 1>;
+    }
+    return nullptr;
+}
+
+template <class T>
+static cudaError_t rs3_launch_t(int shape, int r, const RS3Params& p, int grid, cudaStream_t st)
+{
+    const void* k = rs3_kernel_ptr<T>(shape, r);
+    if (!k) return cudaErrorInvalidValue;
+    void* args[] = {(void*)&p};
+    return cudaLaunchKernel(k, dim3(grid), dim3(kRSThreads), args, 0, st);
+}
+
+template <class T>
+static cudaError_t rs3_occupancy_t(int shape, int r, int* blocks)
+{
+    const void* k = rs3_kernel_ptr<T>(shape, r);
+    if (!k) return cudaErrorInvalidValue;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kRSThreads, 0);
+}
+
 }  // namespace ebisu
 
 #define EBISU_DEFINE_RS_ENTRY(T, NAME)                                                              \
@@ -54,4 +85,9 @@ static cudaError_t rs_occupancy_t(int shape, int r, int depth, bool batch, int* 
         return rs_launch_t<T>(s, r, d, p, g, st);                                                   \
     }                                                                                               \
     cudaError_t rs_occupancy_##NAME(int s, int r, int d, bool bt, int* b) { return rs_occupancy_t<T>(s, r, d, bt, b); } \
+    cudaError_t rs3_launch_##NAME(int s, int r, const RS3Params& p, int g, cudaStream_t st)        \
+    {                                                                                               \
+        return rs3_launch_t<T>(s, r, p, g, st);                                                     \
+    }                                                                                               \
+    cudaError_t rs3_occupancy_##NAME(int s, int r, int* b) { return rs3_occupancy_t<T>(s, r, b); } \
     }

@@ -299,6 +299,38 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
     naive.variant = 1;
     cand.push_back(naive);
     ++n;
+    // The 3D register-streaming build (FP64, depth 1): z segments sized so
+    // that one step has about 1, 2 or 4 tiles per resident warp.
+    if (plan->ndim == 3 && rs3_built((int)plan->esize, plan->shape, plan->radius)) {
+        const DeviceInfo& dv = device_info();
+        int occ = 0;
+        if (rs3_occupancy(plan, &occ) != cudaSuccess || occ < 1) {
+            cudaGetLastError();
+        } else {
+            const int64_t warps = (int64_t)occ * dv.sms * kRSWarps;
+            const int64_t S = kRS3Cols - 2LL * plan->radius, TY = rs3_rows(plan->radius);
+            const int64_t xy = ((plan->n[2] + S - 1) / S) * ((plan->n[1] + TY - 1) / TY);
+            int64_t lastH = -1;
+            for (int k : {1, 2, 4}) {
+                const int64_t ng = std::max<int64_t>(1, (k * warps + xy - 1) / xy);
+                const int64_t H = (plan->n[0] + ng - 1) / ng;
+                if (H == lastH) continue;
+                lastH = H;
+                ebisu_params q{};
+                q.variant = 2;
+                q.depth = 1;
+                q.tile_s = (int32_t)H;
+                q.ctas_per_sm = occ;
+                q.threads = kRSThreads;
+                RSLayout L;
+                if (rs_layout(plan, q, &L) != EBISU_OK) continue;
+                q.tile_x = L.S;
+                q.tile_y = L.TY;
+                cand.push_back(q);
+                ++n;
+            }
+        }
+    }
     // The register-streaming build (2D): both built depths, segments sized so
     // that one temporal block has about 1, 2 or 4 tiles per resident warp.
     if (plan->ndim == 2) {

@@ -111,6 +111,14 @@ def test_register_streaming_params():
     assert p3.rs_depths() == (0, 0)
     with pytest.raises(ebisu.EbisuError):
         p3.set_params(variant=2, depth=4)
+    # 3D: FP64 radius 1 only, depth 1, 62-column strips of 2-row patches
+    p3d = ebisu.Plan(3, (64, 64, 200), 1, 1, [0.03] * 27, ebisu.F64, ebisu.DIRICHLET)
+    assert p3d.rs_depths() == (1, 1)
+    p3d.set_params(variant=2, depth=1, tile_s=16, ctas_per_sm=2)
+    q3 = p3d.params()
+    assert (q3.tile_x, q3.tile_y, q3.tile_s, q3.depth) == (62, 2, 16, 1)
+    with pytest.raises(ebisu.EbisuError):
+        p3d.set_params(variant=2, depth=2)
     pp = ebisu.Plan(2, (100, 100), 0, 1, [0.2] * 5, ebisu.F32, ebisu.PERIODIC)
     with pytest.raises(ebisu.EbisuError):
         pp.set_params(variant=2, depth=pp.rs_depths()[0])

@@ -151,3 +151,69 @@ def test_rs_tuner_may_pick_it():
     assert plan.params().variant in (0, 1, 2)
     y = run(plan, x, 21)
     assert torch.equal(y, run(plan, x, 21, naive=True))
+
+
+# ---- 3D register streaming (FP64, depth 1: the 7-point star, the 27-point box)
+
+@pytest.mark.parametrize("shape,r", [(0, 1), (1, 1), (0, 2)])
+@pytest.mark.parametrize("boundary", [0, 1])
+@pytest.mark.parametrize("tile_s", [0, 7, 16])
+def test_rs3_parity(shape, r, boundary, tile_s):
+    eb = _eb()
+    # several strips (64 - 2r columns), bands and z segments, ragged tails (a
+    # periodic grid's last band must still cover the radius)
+    dims = (37, 45, 150) if boundary == 0 else (37, 46, 150)
+    g, c = synth.problem(3, dims, shape, r, boundary, seed=400 + shape + 2 * boundary + 5 * r)
+    x = torch.from_numpy(g).cuda()
+    plan = eb.Plan(3, dims, shape, r, c, eb.F64, boundary)
+    assert plan.rs_depths() == (1, 1)
+    plan.set_params(variant=2, depth=1, tile_s=tile_s, ctas_per_sm=4)
+    p = plan.params()
+    assert (p.variant, p.tile_x, p.tile_y) == (2, 64 - 2 * r, 2)
+    steps = 5
+    y = run(plan, x, steps)
+    assert torch.equal(y, run(plan, x, steps, naive=True)), "3D register-streaming and naive kernels differ"
+    ref = oracle.run(g, shape, r, c, boundary, steps)
+    pad = r if boundary == 0 else 0
+    assert oracle.rel_linf(y.cpu().numpy(), ref, pad) <= TOL[0]
+    if boundary == 0:
+        m = np.ones(g.shape, bool)
+        m[r:-r, r:-r, r:-r] = False
+        assert np.array_equal(y.cpu().numpy()[m], g[m])
+
+
+@pytest.mark.parametrize("steps", [1, 2, 6])
+def test_rs3_in_place_and_unsupported(steps):
+    eb = _eb()
+    dims = (20, 24, 80)
+    g, c = synth.problem(3, dims, 0, 1, 0, seed=410)
+    plan = eb.Plan(3, dims, 0, 1, c, eb.F64, 0)
+    plan.set_params(variant=2, depth=1, tile_s=8, ctas_per_sm=4)
+    ws = plan.workspace()
+    y = torch.from_numpy(g).cuda()
+    plan.run(y, y, steps, ws)
+    assert plan.sync(ws) == 0
+    ref = oracle.run(g, 0, 1, c, 0, steps)
+    assert oracle.rel_linf(y.cpu().numpy(), ref, 1) <= TOL[0]
+    # no 3D build for the 125-point box or FP32
+    p2 = eb.Plan(3, dims, 1, 2, [0.01] * 125, eb.F64, 0)
+    assert p2.rs_depths() == (0, 0)
+    assert eb.Plan(3, dims, 0, 1, [0.1] * 7, eb.F32, 0).rs_depths() == (0, 0)
+    with pytest.raises(eb.EbisuError):
+        p2.set_params(variant=2, depth=1)
+
+
+def test_rs3_wait_timeout_reports_status(monkeypatch):
+    eb = _eb()
+    monkeypatch.setenv("EBISU_WAIT_TIMEOUT_MS", "200")
+    dims = (16, 16, 70)
+    g, c = synth.problem(3, dims, 1, 1, 0, seed=411)
+    plan = eb.Plan(3, dims, 1, 1, c, eb.F64, 0)
+    plan.set_params(variant=2, depth=1, tile_s=8, ctas_per_sm=4)
+    x = torch.from_numpy(g).cuda()
+    ws = plan.workspace()
+    y = torch.empty_like(x)
+    plan.run_stalled(x, y, 3, ws)
+    assert plan.sync(ws) == eb.ERR_TIMEOUT
+    plan.run(x, y, 3, ws)
+    assert plan.sync(ws) == 0
