@@ -343,7 +343,13 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
         // the short tails form a chain through the levels.
         // (star: the centre row's r edge cells come from the adjacent lanes)
         constexpr int kTail = P - (EXT ? 2 * R + 1 : 1);  // first term on row +r
-        auto level_row = [&](int s, int cs, C(&acc)[4], const bool head) {
+        // The accumulators of levels below t are the queue slots they fill
+        // (the slot's old row is dead by then), so no copy follows the FMAs.
+        C accD[4];  // level t's row (to global memory)
+        auto acc_ref = [&](int s, int cs, int m) -> C& {
+            return (s < D) ? ring[s < D ? s : 0][cs][X0 + m] : accD[m];
+        };
+        auto level_row = [&](int s, int cs, const bool head) {
             C e[EXT ? 1 : 4 + 2 * R];
             if (!EXT && head) {
 #pragma unroll
@@ -365,7 +371,8 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                     C v;
                     if constexpr (EXT) v = ring[s - 1][rs][X0 + m + dx];
                     else v = (dy == 0) ? e[R + m + dx] : ring[s - 1][rs][m];
-                    acc[m] = (k == 0) ? Dt::mul(ck, v) : Dt::fma(ck, v, acc[m]);
+                    C& a = acc_ref(s, cs, m);
+                    a = (k == 0) ? Dt::mul(ck, v) : Dt::fma(ck, v, a);
                 }
             }
         };
@@ -444,25 +451,24 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                             for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
                             load_row2(stage[u % PF], yi + PF, G);
                         }
-                        C acc[D][4];
 #pragma unroll
-                        for (int s = 1; s <= D; ++s) level_row(s, ((u - s * R) % U + U) % U, acc[s - 1], true);
+                        for (int s = 1; s <= D; ++s) level_row(s, ((u - s * R) % U + U) % U, true);
 #pragma unroll
                         for (int s = 1; s <= D; ++s) {
                             const int y = yi - s * R;                  // row of level s computed now
                             const int cs = ((u - s * R) % U + U) % U;  // queue slot of row y
                             C o[4];
-                            level_row(s, cs, acc[s - 1], false);
+                            level_row(s, cs, false);
                             if constexpr (G) {
                                 const bool copy = (s > deff) || (!per && (y < 0 || y >= n0i));
                                 const unsigned keep = copy ? 0xfu : padm;
 #pragma unroll
                                 for (int m = 0; m < 4; ++m)
                                     o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m]
-                                                              : Dt::widen(Dt::narrow(acc[s - 1][m]));
+                                                              : Dt::widen(Dt::narrow(acc_ref(s, cs, m)));
                             } else {
 #pragma unroll
-                                for (int m = 0; m < 4; ++m) o[m] = Dt::widen(Dt::narrow(acc[s - 1][m]));
+                                for (int m = 0; m < 4; ++m) o[m] = Dt::widen(Dt::narrow(acc_ref(s, cs, m)));
                             }
                             put_row(s, cs, y, o);
                         }
@@ -494,9 +500,8 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                         for (int q = 0; q < RW; ++q) ring[0][u][q] = stage[u % PF][q];
                         load_row(stage[u % PF], yi + PF);
                     }
-                    C acc[D][4];
 #pragma unroll
-                    for (int s = 1; s <= D; ++s) level_row(s, ((u - s * R) % U + U) % U, acc[s - 1], true);
+                    for (int s = 1; s <= D; ++s) level_row(s, ((u - s * R) % U + U) % U, true);
 #pragma unroll
                     for (int s = 1; s <= D; ++s) {
                         const int y = yi - s * R;                  // row of level s computed now
@@ -506,10 +511,10 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                         const bool copy = (s > deff) || (!per && (y < 0 || y >= n0i));
                         const unsigned keep = copy ? 0xfu : padm;
                         C o[4];
-                        level_row(s, cs, acc[s - 1], false);
+                        level_row(s, cs, false);
 #pragma unroll
                         for (int m = 0; m < 4; ++m)
-                            o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m] : Dt::widen(Dt::narrow(acc[s - 1][m]));
+                            o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m] : Dt::widen(Dt::narrow(acc_ref(s, cs, m)));
                         put_row(s, cs, y, o);
                     }
                 }
