@@ -32,6 +32,16 @@ STENCILS = [("star", 0, 1), ("star", 0, 2), ("star", 0, 3), ("box", 1, 1), ("box
 FP64_PEAK_FLOPS = 1.25e12  # nominal GB300 FP64 rate (vector = tensor on this part)
 
 
+# DRAM bytes per cell update measured by ncu for a kernel build
+# (dram__bytes_read.sum + dram__bytes_write.sum of a capture, divided by the
+# capture's cell updates; the traffic grows in proportion with cells x steps
+# at the depth the bench runs).  Only for builds unchanged since the capture.
+TRAFFIC_BYTES_PER_UPDATE = {
+    # profiles/tb_kernel_fp64_2d_box_r2_4096.md: 1.081 GB / (4096^2 x 4)
+    "tb_kernel<double,2D,box r2>": 1.081e9 / (4096 * 4096 * 4),
+}
+
+
 def hbm_peak():
     """Measured copy bandwidth (bytes/s) of this machine's GPUs, else the
     profiling recipe's fallback figure."""
@@ -533,6 +543,9 @@ def main():
         d["kernel"] = KERNEL_NAMES[p["plan"].params().variant]
     dom = max(per, key=lambda d: d["ms_per_launch"])
     achieved = dom["tflops"]
+    dom_name = f"{dom['kernel']}<double,2D,{dom['stencil']}>"
+    bpu = TRAFFIC_BYTES_PER_UPDATE.get(dom_name)
+    dom_traffic = None if bpu is None else bpu * cells * steps  # bytes per launch
 
     # end to end through the public API with host buffers: H2D input, solve,
     # D2H result grid, every step
@@ -621,8 +634,8 @@ def main():
                    "l2": "inputs larger than L2 (537 MB per grid, 129 MB L2)",
                    "parallelism": f"replicas x{ws_n}"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved * 1e12 / FP64_PEAK_FLOPS, "traffic": None,
-                     "kernel": f"{dom['kernel']}<double,2D,{dom['stencil']}>",
+                     "frac": achieved * 1e12 / FP64_PEAK_FLOPS, "traffic": dom_traffic,
+                     "kernel": dom_name,
                      "peak_source": "nominal FP64 rate of the profiling recipe's table; live probe "
                                     f"{probe['f64_flops'] / 1e12:.3f} TFLOP/s"},
         "per_stencil": per,

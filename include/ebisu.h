@@ -81,14 +81,18 @@ enum ebisu_boundary { EBISU_DIRICHLET = 0, EBISU_PERIODIC = 1 };
  *   variant        : 0 = temporally blocked persistent kernel (shared-
  *                    memory queues), 1 = naive one-step-per-launch kernel
  *                    (ebisu_run then takes the naive path), 2 = register-
- *                    streaming temporally blocked kernel (2D only): one warp
- *                    per 128-column strip, every time level in registers;
- *                    depth must be one of ebisu_plan_rs_depths(), tile_s is
- *                    the rows per strip segment, ctas_per_sm caps the
- *                    resident 128-thread CTAs, and tile_x is set to the
- *                    strip's output width 128 - 2*depth*radius.  Batches and
- *                    the server always run variant 0 with the last variant-0
- *                    parameters the plan held. */
+ *                    streaming temporally blocked kernel: in 2D one warp per
+ *                    128-column strip, every time level in registers; in 3D
+ *                    (FP64, radius 1 and the 13-point star, depth 1) one warp
+ *                    per 64-column x 2-row patch streamed along z.  depth
+ *                    must be one of ebisu_plan_rs_depths(), tile_s is the
+ *                    rows (2D) or planes (3D) per segment, ctas_per_sm caps
+ *                    the resident 128-thread CTAs, and tile_x / tile_y are
+ *                    set to the strip's output width (128 - 2*depth*radius;
+ *                    3D: 64 - 2*radius) and the patch's rows.  Batches run
+ *                    2D variant-2 plans with the register-streaming kernel
+ *                    and every other plan with variant 0, using the last
+ *                    variant-0 parameters the plan held. */
 typedef struct ebisu_params {
     int32_t tile_x;
     int32_t tile_y;
@@ -146,8 +150,9 @@ int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* p);
 
 /* Temporal depths built for the register-streaming kernel (variant 2) of
  * this plan's stencil and storage type (Section 4's temporal blocking with
- * the per-level queues held in registers): *shallow <= *deep.  Both are 0
- * for 3D plans (no such kernel).  Host only; never fails for a valid plan. */
+ * the per-level queues held in registers): *shallow <= *deep.  3D plans: 1
+ * and 1 for the FP64 7- and 13-point stars and 27-point box, else 0 and 0
+ * (no such kernel).  Host only; never fails for a valid plan. */
 int ebisu_plan_rs_depths(ebisu_plan_t plan, int* shallow, int* deep);
 
 /* Bytes of device workspace a run of this plan needs: a control block plus
