@@ -258,6 +258,65 @@ def run_set3d(args):
     print(json.dumps({"workload": f"3D FP64 stencil set, {n}^3, {steps} steps", "rows": rows}), flush=True)
 
 
+def run_paper_sizes(args):
+    """The paper's own benchmark stencils at its domain sizes (Table 2): the
+    2D j2d5pt (8352^2), j2d9pt (9-point star, 8064^2), j2d9pt-gol (9-point
+    box, 8784^2), j2d25pt (8640^2) and the 3D j3d7pt, j3d13pt, j3d27pt
+    (2560 x 288 x 384), Dirichlet, in FP64 (the paper's precision) and FP32;
+    1000 steps in 2D, 200 in 3D; the kernel the tuner picks, against the
+    naive kernel on the same grid.  (j3d17pt and poisson: the paper gives no
+    offset sets.)"""
+    import torch
+    from paper_2305_07390_gb300 import ebisu, synth
+    stream = torch.cuda.current_stream()
+    sh = ebisu.current_stream_handle()
+    rows = []
+    cases = [("j2d5pt", 2, (8352, 8352), 0, 1, 1000), ("j2d9pt", 2, (8064, 8064), 0, 2, 1000),
+             ("j2d9pt-gol", 2, (8784, 8784), 1, 1, 1000), ("j2d25pt", 2, (8640, 8640), 1, 2, 1000),
+             ("j3d7pt", 3, (2560, 288, 384), 0, 1, 200), ("j3d13pt", 3, (2560, 288, 384), 0, 2, 200),
+             ("j3d27pt", 3, (2560, 288, 384), 1, 1, 200)]
+    for name, nd, dims, shape, r, steps in cases:
+        g, c = synth.problem(nd, dims, shape, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED + 17 * r + shape)
+        for dname, dt in (("f64", ebisu.F64), ("f32", ebisu.F32)):
+            plan = ebisu.Plan(nd, dims, shape, r, c, dt, ebisu.DIRICHLET)
+            x = torch.from_numpy(g).to(ebisu.torch_dtype(dt)).cuda()
+            y = torch.empty_like(x)
+            ws = plan.workspace()
+            plan.tune(x, y, 32 if nd == 2 else 8, ws, max_candidates=args.tune)
+            q = plan.params()
+            pref = q.variant
+            if q.variant == 1:
+                plan.set_params(variant=q.fused_variant)
+            plan.run(x, y, steps, ws, stream=sh)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            plan.run(x, y, steps, ws, stream=sh)
+            b.record(stream)
+            b.synchronize()
+            assert plan.sync(ws) == 0
+            ms = a.elapsed_time(b)
+            ns = min(steps, 50)
+            a.record(stream)
+            plan.run(x, y, ns, ws, stream=sh, naive=True)
+            b.record(stream)
+            b.synchronize()
+            cells = 1
+            for d_ in dims:
+                cells *= d_
+            P = npoints(shape, r) if nd == 2 else npoints3(shape, r)
+            rate = cells * steps / (ms * 1e-3)
+            rows.append({"stencil": name, "dtype": dname, "dims": list(dims), "steps": steps, "points": P,
+                         "cell_updates_per_s": rate, "tflops": rate * 2 * P / 1e12,
+                         "naive_cell_updates_per_s": cells * ns / (a.elapsed_time(b) * 1e-3),
+                         "tuner_preferred": VARIANT_NAMES[pref], "kernel": KERNEL_NAMES[plan.params().variant],
+                         "params": plan.params().as_dict()})
+            print(json.dumps(rows[-1]), flush=True)
+            del x, y, ws, plan
+            torch.cuda.empty_cache()
+    print(json.dumps({"workload": "the paper's stencils at its domain sizes (Table 2), FP64 and FP32",
+                      "rows": rows}), flush=True)
+
+
 def npoints3(shape, r):
     return 6 * r + 1 if shape == 0 else (2 * r + 1) ** 3
 
@@ -418,10 +477,11 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="--case: storage type")
     ap.add_argument("--params", default="", help="--case: plan parameters, k=v,k=v")
     ap.add_argument("--naive", action="store_true", help="--case: the one-step-per-launch kernel")
-    ap.add_argument("--workload", default="set", choices=["set", "set3d", "batch", "serve"],
-                    help="set: the FP64 2D stencil set (default, the headline line); batch: 512 uneven "
-                         "2D 9-point box grids in one persistent launch per dtype; serve: Poisson arrivals "
-                         "through the serving loop")
+    ap.add_argument("--workload", default="set", choices=["set", "set3d", "batch", "serve", "paper"],
+                    help="set: the FP64 2D stencil set (default, the headline line); set3d: the FP64 3D "
+                         "set; batch: 512 uneven 2D 9-point box grids in one persistent launch per dtype; "
+                         "serve: Poisson arrivals through the serving loop; paper: the paper's stencils at "
+                         "its domain sizes")
     ap.add_argument("--serve-rates", default="5,10,20,50,100,200,500,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
@@ -431,6 +491,8 @@ def main():
         return run_batch(args)
     if args.workload == "set3d":
         return run_set3d(args)
+    if args.workload == "paper":
+        return run_paper_sizes(args)
     if args.workload == "serve":
         return run_serve(args)
     if args.warmup < 3:
