@@ -86,9 +86,12 @@ constexpr int rs_depth(int esize, int shape /*0 star, 1 box*/, int r, int which)
 // the rows of a warp's patch.
 constexpr bool rs3_built(int esize, int shape, int r)
 {
-    return esize == 8 && (r == 1 || (shape == 0 && r == 2));
+    return (esize == 8 && (r == 1 || (shape == 0 && r == 2))) || (esize == 4 && shape == 0 && r == 1);
 }
-constexpr int rs3_rows(int r) { return r <= 2 ? 2 : 1; }
+// rows of a warp's patch (FP64 depth 1: 2; FP32 temporally blocked: 4)
+constexpr int rs3_rows(int esize) { return esize == 8 ? 2 : 4; }
+// temporal depths built (FP64: 1; FP32 7-point star: 2 and 3)
+constexpr int rs3_depth(int esize, int which) { return esize == 8 ? 1 : (which ? 3 : 2); }
 constexpr int kRS3Cols = 64;  // columns a warp holds (32 lanes x 2)
 
 // Depth the register-streaming build defaults to (FP32/BF16 storage): the
@@ -148,7 +151,8 @@ struct RS3Params {
     int32_t S;           // output columns per strip (64 - 2 * radius)
     int32_t H;           // output planes per z segment
     int32_t nstrips, nbands, nsegs;
-    int32_t nblocks;     // = steps (depth 1)
+    int32_t nblocks;     // ceil(steps / depth)
+    int32_t depth_last;  // steps done by the last block (<= depth)
     int32_t debug_stall;
     double coef[kMaxPoints];
     float coef_f[kMaxPoints];

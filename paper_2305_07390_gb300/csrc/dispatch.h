@@ -39,8 +39,8 @@ struct PadParams {
 #define EBISU_DECLARE_RS_ENTRY(NAME)                                                               \
     cudaError_t rs_launch_##NAME(int s, int r, int d, const RSParams& p, int g, cudaStream_t st);   \
     cudaError_t rs_occupancy_##NAME(int s, int r, int d, bool batch, int* b);                      \
-    cudaError_t rs3_launch_##NAME(int s, int r, const RS3Params& p, int g, cudaStream_t st);       \
-    cudaError_t rs3_occupancy_##NAME(int s, int r, int* b);
+    cudaError_t rs3_launch_##NAME(int s, int r, int d, const RS3Params& p, int g, cudaStream_t st); \
+    cudaError_t rs3_occupancy_##NAME(int s, int r, int d, int* b);
 
 EBISU_DECLARE_RS_ENTRY(f64)
 EBISU_DECLARE_RS_ENTRY(f32)

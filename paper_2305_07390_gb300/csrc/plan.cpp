@@ -106,23 +106,27 @@ size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q)
 // rows, z segments of H planes; depth 1 only.
 static int rs3_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L)
 {
-    const int r = p->radius;
-    if (!rs3_built((int)p->esize, p->shape, r) || q.depth != 1) return EBISU_ERR_UNSUPPORTED;
+    const int r = p->radius, es = (int)p->esize;
+    if (!rs3_built(es, p->shape, r)) return EBISU_ERR_UNSUPPORTED;
+    if (q.depth != rs3_depth(es, 0) && q.depth != rs3_depth(es, 1)) return EBISU_ERR_UNSUPPORTED;
     const int64_t n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
     if (n0 + 2 * p->pad > (1LL << 30) || n1 + 2 * p->pad > (1LL << 30) || n2 + 2 * p->pad > (1LL << 30))
         return EBISU_ERR_UNSUPPORTED;
     const bool per = p->boundary == EBISU_PERIODIC;
     // the kernel wraps a periodic index at most once
     if (per && (n0 < 16 || n1 < 16 || n2 < 72)) return EBISU_ERR_UNSUPPORTED;
-    const int S = kRS3Cols - 2 * r, TY = rs3_rows(r);
+    const int dr = q.depth * r;
+    const int S = kRS3Cols - 2 * dr, TY = rs3_rows(es);
     const int64_t H = (q.tile_s <= 0) ? n0 : std::min<int64_t>(q.tile_s, n0);
     const int64_t ns = (n2 + S - 1) / S, nb = (n1 + TY - 1) / TY, ng = (n0 + H - 1) / H;
-    // a tile's inputs reach r cells into its neighbours and no further
-    if ((ng > 1 && H < r) || TY < r) return EBISU_ERR_UNSUPPORTED;
-    if (per && ((ns > 1 && n2 - (ns - 1) * S < r) || (nb > 1 && n1 - (nb - 1) * TY < r) ||
-                (ng > 1 && n0 - (ng - 1) * H < r)))
+    // a tile's inputs reach depth*r cells into its neighbours and no further
+    if ((ng > 1 && H < dr) || TY < dr || S < dr) return EBISU_ERR_UNSUPPORTED;
+    if (per && ((ns > 1 && n2 - (ns - 1) * S < dr) || (nb > 1 && n1 - (nb - 1) * TY < dr) ||
+                (ng > 1 && n0 - (ng - 1) * H < dr)))
         return EBISU_ERR_UNSUPPORTED;
     if (ns * nb * ng > kRSMaxTiles) return EBISU_ERR_UNSUPPORTED;
+    // the FP32 build addresses within a plane with 32-bit offsets
+    if ((n1 + 2 * p->pad) * (n2 + 2 * p->pad) >= (1LL << 31)) return EBISU_ERR_UNSUPPORTED;
     if (L) {
         L->S = S;
         L->H = (int)H;
@@ -312,16 +316,22 @@ cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int
     }
 }
 
-cudaError_t rs3_launch(const ebisu_plan_s* p, const RS3Params& prm, int grid, cudaStream_t st)
+cudaError_t rs3_launch(const ebisu_plan_s* p, int depth, const RS3Params& prm, int grid, cudaStream_t st)
 {
-    if (p->dtype != EBISU_F64) return cudaErrorInvalidValue;
-    return rs3_launch_f64(p->shape, p->radius, prm, grid, st);
+    switch (p->dtype) {
+    case EBISU_F64: return rs3_launch_f64(p->shape, p->radius, depth, prm, grid, st);
+    case EBISU_F32: return rs3_launch_f32(p->shape, p->radius, depth, prm, grid, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
-cudaError_t rs3_occupancy(const ebisu_plan_s* p, int* blocks)
+cudaError_t rs3_occupancy(const ebisu_plan_s* p, int depth, int* blocks)
 {
-    if (p->dtype != EBISU_F64) return cudaErrorInvalidValue;
-    return rs3_occupancy_f64(p->shape, p->radius, blocks);
+    switch (p->dtype) {
+    case EBISU_F64: return rs3_occupancy_f64(p->shape, p->radius, depth, blocks);
+    case EBISU_F32: return rs3_occupancy_f32(p->shape, p->radius, depth, blocks);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, bool batch, int* blocks)
@@ -368,9 +378,9 @@ int64_t fill_rs_grid(const ebisu_plan_s* p, const RSLayout& L, const void* in, v
     return nb;
 }
 
-// A run of the 3D register-streaming build (depth 1: one temporal block per
-// step).  The kernel never writes pad cells: the buffers it writes first get
-// the input's pad from a copy kernel.
+// A run of the 3D register-streaming build (FP64: depth 1; FP32: depth 2 or
+// 3).  The kernel never writes pad cells: the buffers it writes first get the
+// input's pad from a copy kernel.
 static int run_rs3(ebisu_plan_t p, const void* in, void* out, int64_t steps, void* ws, cudaStream_t st,
                    int debug_stall)
 {
@@ -378,7 +388,8 @@ static int run_rs3(ebisu_plan_t p, const void* in, void* out, int64_t steps, voi
     RSLayout L;
     int rc = rs_layout(p, q, &L);
     if (rc != EBISU_OK) return rc;
-    const int64_t nb = steps;
+    const int D = q.depth;
+    const int64_t nb = (steps + D - 1) / D;
     const int64_t ntiles = (int64_t)L.nstrips * L.nbands * L.nsegs;
     const DeviceInfo& dv = device_info();
     if (nb * ntiles + 64LL * 16 * dv.sms * kRSWarps >= (1LL << 32)) return EBISU_ERR_UNSUPPORTED;
@@ -421,18 +432,19 @@ static int run_rs3(ebisu_plan_t p, const void* in, void* out, int64_t steps, voi
     prm.nbands = L.nbands;
     prm.nsegs = L.nsegs;
     prm.nblocks = (int32_t)nb;
+    prm.depth_last = (int32_t)(steps - (nb - 1) * D);
     prm.debug_stall = debug_stall;
     for (int k = 0; k < p->npts; ++k) {
         prm.coef[k] = p->coef[k];
         prm.coef_f[k] = (float)p->coef[k];
     }
     int occ = 0;
-    e = rs3_occupancy(p, &occ);
+    e = rs3_occupancy(p, D, &occ);
     if (e != cudaSuccess) return fail_cuda(e);
     if (occ < 1) return EBISU_ERR_UNSUPPORTED;
     int64_t grid = (int64_t)std::min(occ, q.ctas_per_sm) * dv.sms;
     grid = std::min<int64_t>(grid, (prm.nitems + kRSWarps - 1) / kRSWarps);
-    e = rs3_launch(p, prm, (int)grid, st);
+    e = rs3_launch(p, D, prm, (int)grid, st);
     if (e != cudaSuccess) return fail_cuda(e);
     return EBISU_OK;
 }
@@ -646,7 +658,10 @@ int ebisu_plan_rs_depths(ebisu_plan_t plan, int* shallow, int* deep)
 {
     if (!plan || !shallow || !deep) return EBISU_ERR_INVALID_ARG;
     if (plan->ndim != 2) {
-        *shallow = *deep = rs3_built((int)plan->esize, plan->shape, plan->radius) ? 1 : 0;
+        const int es = (int)plan->esize;
+        const bool b = rs3_built(es, plan->shape, plan->radius);
+        *shallow = b ? rs3_depth(es, 0) : 0;
+        *deep = b ? rs3_depth(es, 1) : 0;
         return EBISU_OK;
     }
     *shallow = rs_depth((int)plan->esize, plan->shape, plan->radius, 0);

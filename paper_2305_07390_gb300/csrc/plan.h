@@ -89,8 +89,8 @@ struct RSLayout {
 int rs_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L);
 cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int grid, cudaStream_t st);
 cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, bool batch, int* blocks);
-cudaError_t rs3_launch(const ebisu_plan_s* p, const RS3Params& prm, int grid, cudaStream_t st);
-cudaError_t rs3_occupancy(const ebisu_plan_s* p, int* blocks);
+cudaError_t rs3_launch(const ebisu_plan_s* p, int depth, const RS3Params& prm, int grid, cudaStream_t st);
+cudaError_t rs3_occupancy(const ebisu_plan_s* p, int depth, int* blocks);
 // Fill the descriptor of one register-streaming run of `steps` >= 1 steps
 // (src0: the first block's input; pads of the other written buffers are
 // filled by the kernel).  Returns the number of temporal blocks.

@@ -1,0 +1,278 @@
+// rs3t_kernel.cuh -- register-streaming temporally blocked kernel for 3D
+// 7-point star grids in FP32 storage (temporal depth t >= 2).
+//
+// FP32 3D stencils are memory-bound at depth 1 (the naive kernel streams at
+// the HBM rate), so they need the paper's temporal blocking (Section 4) with
+// t > 1.  This kernel does it in registers, like rs_kernel.cuh in 2D:
+//  * One warp owns a 64-column x 4-row output patch of the xy plane -- lane l
+//    holds columns 2l, 2l+1 -- and streams it along z (N.5-D streaming).
+//  * Time level s (0 = input) covers the patch's rows widened by t - s rows
+//    on each side (overlapped tiling along y inside the warp, Section 2.1.2)
+//    and all 64 columns (along x the valid part shrinks by one column per
+//    level: strips advance by 64 - 2t columns).  Each level s < t keeps its
+//    last three planes in registers (the circular multi-queue of Section
+//    4.2, along z; the plane loop is unrolled three times so every queue
+//    slot is a fixed register) and computes plane z - s when level 0
+//    receives plane z (lag 1 per level: one warp owns the whole patch, so
+//    no barrier separates the levels).
+//  * x neighbours of the centre row come from the adjacent lanes by warp
+//    shuffles; the other six neighbours are in this lane's registers.
+//  * Level-0 planes are staged 4 planes ahead in shared memory by per-lane
+//    cp.async (each lane copies and later reads back only its own cells).
+//  * Dirichlet pad cells keep their input value at every level (copied from
+//    the level below); levels past the last block's depth pass values on.
+//  * Tiles (strip, band, z segment) of block b wait only for their 3 x 3 x 3
+//    neighbours of block b-1 (a tile's inputs reach t cells past its output,
+//    at most one patch, strip or segment away).
+#pragma once
+#include <type_traits>
+
+#include "common.h"
+#include "stencil.cuh"
+
+namespace ebisu {
+
+template <class T, int D>
+struct RS3TGeom {
+    using C = typename DT<T>::C;
+    static constexpr int VX = 2;   // columns per lane
+    static constexpr int TY = 4;   // output rows per warp
+    static constexpr int U = 3;    // planes queued per level (2r + 1, r = 1)
+    static constexpr int PFS = 4;  // level-0 planes in flight (shared memory)
+    static constexpr int rows(int s) { return TY + 2 * (D - s); }  // rows of level s
+    static constexpr int off(int s)  // first register of level s's queue
+    {
+        int o = 0;
+        for (int q = 0; q < s; ++q) o += U * rows(q) * VX;
+        return o;
+    }
+    static constexpr int RING = off(D);  // levels 0 .. D-1
+    static constexpr int regs() { return RING + rows(1) * VX + 80; }
+    static constexpr int minb()
+    {
+        const int e = (regs() + 7) & ~7;
+        const int b = 65536 / (kRSThreads * e);
+        return b < 1 ? 1 : (b > 8 ? 8 : b);
+    }
+};
+
+template <class T, int D>
+__device__ __forceinline__ void rs3t_cp_async(T* smem, const T* gmem, int src_size)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "r"(src_size) : "memory");
+}
+
+template <class T, int D>
+__global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, D>::minb()) rs3t_kernel(const __grid_constant__ RS3Params prm)
+{
+    static_assert(sizeof(T) == 4, "shared-memory staging copies 4-byte elements");
+    using G = RS3TGeom<T, D>;
+    using Dt = DT<T>;
+    using C = typename Dt::C;
+    using St = Stencil<3, kStar, 1>;
+    constexpr int P = St::P;
+    constexpr int VX = G::VX, TY = G::TY, U = G::U, PFS = G::PFS;
+    constexpr int Y0 = G::rows(0);  // rows loaded per plane
+    constexpr auto OFF = St::kOff;  // (dz, dy, dx) in canonical order
+    constexpr unsigned FULL = 0xffffffffu;
+
+    const int lane = threadIdx.x & 31;
+    Control* const ctl = prm.ctl;
+    const bool per = prm.periodic != 0;
+    const int n0 = (int)prm.n[0], n1 = (int)prm.n[1], n2 = (int)prm.n[2];
+    const int pad = prm.pad;
+    const int64_t lds = prm.lds, ld1 = prm.ld1;
+    const int S = prm.S, H = prm.H, nstrips = prm.nstrips, nbands = prm.nbands, nsegs = prm.nsegs;
+    const long long ntiles = (long long)nstrips * nbands * nsegs;
+
+    C ring[G::RING];
+    // queue register of (level s < D, slot, row, column)
+    auto Q = [&](int s, int slot, int row, int v) -> C& {
+        return ring[G::off(s) + (slot * G::rows(s) + row) * VX + v];
+    };
+    __shared__ __align__(16) T s_stage[kRSWarps * PFS * 32 * Y0 * VX];
+    T* const my_stage = s_stage + ((threadIdx.x >> 5) * PFS * 32 + lane) * (Y0 * VX);
+
+    for (;;) {
+        long long it = -1;
+        if (lane == 0 && *(volatile int*)&ctl->status == 0) it = (long long)atomicAdd(&ctl->next_item, 1u);
+        it = __shfl_sync(FULL, it, 0);
+        if (it < 0 || it >= prm.nitems) return;
+        const int blk = (int)(it / ntiles);
+        const int tile = (int)(it - (long long)blk * ntiles);
+        const int strip = tile % nstrips;
+        const int band = (tile / nstrips) % nbands;
+        const int seg = tile / (nstrips * nbands);
+
+        // ---- wait for the 3 x 3 x 3 neighbouring tiles of the previous block ---
+        int ok = 1;
+        if (lane < 27 && (blk > 0 || prm.debug_stall)) {
+            int sz = seg + lane / 9 - 1, sy = band + (lane / 3) % 3 - 1, sx = strip + lane % 3 - 1;
+            bool exists = true;
+            if (per) {
+                sz = (sz + nsegs) % nsegs;
+                sy = (sy + nbands) % nbands;
+                sx = (sx + nstrips) % nstrips;
+            } else {
+                exists = sz >= 0 && sz < nsegs && sy >= 0 && sy < nbands && sx >= 0 && sx < nstrips;
+            }
+            if (exists) {
+                const unsigned target = (unsigned)blk + (prm.debug_stall ? 1u : 0u);
+                const unsigned* cnt = &ctl->done[((int64_t)sz * nbands + sy) * nstrips + sx];
+                if (ld_acquire_u32(cnt) < target) {
+                    const uint64_t t0 = global_ns();
+                    unsigned ns = 32;
+                    while (ld_acquire_u32(cnt) < target) {
+                        if (*(volatile int*)&ctl->status != 0) { ok = 0; break; }
+                        if (global_ns() - t0 > (uint64_t)prm.timeout_ns) {
+                            atomicCAS(&ctl->status, 0, 6 /* EBISU_ERR_TIMEOUT */);
+                            atomicExch(&ctl->wait_where, (unsigned)it);
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(ns);
+                        ns = ns < 1024 ? ns * 2 : ns;
+                    }
+                }
+            }
+        }
+        if (!__all_sync(FULL, ok)) return;
+
+        // ---- geometry ----------------------------------------------------------
+        const bool lastb = (blk == prm.nblocks - 1);
+        const int deff = lastb ? prm.depth_last : D;  // levels above deff pass values on
+        const bool dst_is_out = ((prm.nblocks - 1 - blk) & 1) == 0;
+        T* const dst = reinterpret_cast<T*>(dst_is_out ? prm.out : prm.ws);
+        const T* const src = (blk == 0) ? reinterpret_cast<const T*>(prm.src0)
+                                        : reinterpret_cast<const T*>(dst_is_out ? prm.ws : prm.out);
+        const int xs = strip * S, xe = min(xs + S, n2);
+        const int cb = xs - D + VX * lane;  // this lane's first column
+        const int ya = band * TY;           // first output row
+        const int za = seg * H, zb = min(za + H, n0);
+        const int lo0 = per ? za - D : max(za - D, -pad);
+        const int hi0 = per ? zb + D : min(zb + D, n0 + pad);
+        const int niter = zb + D - lo0;  // level D's last plane zb-1 arrives last
+        // level-0 rows ya - D .. ya - D + Y0 - 1 and this lane's columns:
+        // which exist, where they are stored
+        unsigned rowok = 0, colok = 0, padc = 0, outc = 0;
+#pragma unroll
+        for (int i = 0; i < Y0; ++i) {
+            const int y = ya - D + i;
+            if (per || (y >= -pad && y < n1 + pad)) rowok |= 1u << i;
+        }
+#pragma unroll
+        for (int v = 0; v < VX; ++v) {
+            const int c = cb + v;
+            if (per || (c >= -pad && c < n2 + pad)) colok |= 1u << v;
+            if (!per && (c < 0 || c >= n2)) padc |= 1u << v;
+            if (c >= xs && c < xe) outc |= 1u << v;
+        }
+        // in-plane stored offsets (32-bit: the host keeps a plane below 2^31
+        // elements) of loaded row i and of this lane's column v
+        int rowoff[Y0], coloff[VX];
+#pragma unroll
+        for (int i = 0; i < Y0; ++i) {
+            int y = ya - D + i;
+            if (per) y = (y < 0) ? y + n1 : (y >= n1 ? y - n1 : y);  // one wrap at most (n1 >= 16)
+            rowoff[i] = (y + pad) * (int)ld1;
+        }
+#pragma unroll
+        for (int v = 0; v < VX; ++v) {
+            int c = cb + v;
+            if (per) c = (c < 0) ? c + n2 : (c >= n2 ? c - n2 : c);  // one wrap at most (n2 >= 72)
+            coloff[v] = c + pad;
+        }
+        auto issue_plane = [&](int slot, int z) {
+            T* const sp = my_stage + slot * (32 * Y0 * VX);
+            if (z < hi0) {
+                const int zw = per ? ((z < 0) ? z + n0 : (z >= n0 ? z - n0 : z)) : z + pad;
+                const T* const pp = src + (int64_t)zw * lds;
+#pragma unroll
+                for (int i = 0; i < Y0; ++i)
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        const bool okc = ((rowok >> i) & (colok >> v)) & 1u;
+                        rs3t_cp_async<T, D>(sp + i * VX + v, okc ? pp + (rowoff[i] + coloff[v]) : src, okc ? 4 : 0);
+                    }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+
+        // ---- stream along z ------------------------------------------------------
+        // Every level computes a plane at every step; planes and rows outside a
+        // level's region hold garbage that no kept value depends on.
+#pragma unroll
+        for (int q = 0; q < PFS; ++q) issue_plane(q, lo0 + q);
+        for (int j0 = 0; j0 < niter; j0 += U) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int zi = lo0 + j0 + u;  // plane arriving at level 0
+                {
+                    const int slot = (j0 + u) & (PFS - 1);
+                    asm volatile("cp.async.wait_group %0;" ::"n"(PFS - 1) : "memory");
+                    const T* const sp = my_stage + slot * (32 * Y0 * VX);
+#pragma unroll
+                    for (int i = 0; i < Y0; ++i)
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) Q(0, u, i, v) = Dt::widen(sp[i * VX + v]);
+                    issue_plane(slot, zi + PFS);
+                }
+#pragma unroll
+                for (int s = 1; s <= D; ++s) {
+                    const int zs = zi - s;                      // plane of level s computed now
+                    const int cs = ((u - s) % U + U) % U;       // queue slot of plane zs
+                    const int sp_ = ((u - s - 1) % U + U) % U;  // slot of plane zs - 1
+                    const int sn = ((u - s + 1) % U + U) % U;   // slot of plane zs + 1
+                    const int ys = ya - (D - s);  // global row of level s's row 0
+                    const bool copy = (s > deff) || (!per && (zs < 0 || zs >= n0));
+#pragma unroll
+                    for (int i = 0; i < G::rows(s); ++i) {
+                        const int ib = i + 1;  // the same row in level s-1
+                        // centre row's x neighbours
+                        const C l1 = __shfl_up_sync(FULL, Q(s - 1, cs, ib, VX - 1), 1);
+                        const C r0 = __shfl_down_sync(FULL, Q(s - 1, cs, ib, 0), 1);
+                        const int y = ys + i;
+                        const bool prow = !per && (y < 0 || y >= n1);
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            // canonical order: (-1,0,0) (0,-1,0) (0,0,-1) (0,0,0) (0,0,1) (0,1,0) (1,0,0)
+                            C acc;
+#pragma unroll
+                            for (int k = 0; k < P; ++k) {
+                                const int dz = OFF.ds[k], dy = OFF.d1[k], dx = OFF.d2[k];
+                                C val;
+                                if (dz != 0) {
+                                    val = Q(s - 1, dz < 0 ? sp_ : sn, ib, v);
+                                } else if (dy != 0) {
+                                    val = Q(s - 1, cs, ib + dy, v);
+                                } else {
+                                    const int cx = v + dx;
+                                    val = (cx < 0) ? l1 : (cx >= VX ? r0 : Q(s - 1, cs, ib, cx));
+                                }
+                                const C ck = prm.coef_f[k];
+                                acc = (k == 0) ? Dt::mul(ck, val) : Dt::fma(ck, val, acc);
+                            }
+                            const bool keep = copy || prow || ((padc >> v) & 1u);
+                            const C o = keep ? Q(s - 1, cs, ib, v) : Dt::widen(Dt::narrow(acc));
+                            if (s < D) {
+                                Q(s < D ? s : 0, cs, i, v) = o;
+                            } else if (zs >= za && zs < zb && i < TY && ya + i < n1 && ((outc >> v) & 1u)) {
+                                T* const pz = dst + (per ? (int64_t)zs * lds : (int64_t)(zs + pad) * lds);
+                                pz[rowoff[D + i] + coloff[v]] = Dt::narrow(o);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");  // the slots are reused by the next item
+
+        // ---- publish completion of this tile -------------------------------------
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) red_release_add_u32(&ctl->done[tile], 1u);
+    }
+}
+
+}  // namespace ebisu

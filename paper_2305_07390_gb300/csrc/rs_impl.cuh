@@ -5,6 +5,7 @@
 
 #include "dispatch.h"
 #include "rs3_kernel.cuh"
+#include "rs3t_kernel.cuh"
 #include "rs_kernel.cuh"
 
 namespace ebisu {
@@ -46,32 +47,36 @@ static cudaError_t rs_occupancy_t(int shape, int r, int depth, bool batch, int* 
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kRSThreads, 0);
 }
 
-// 3D (depth 1): the 7- and 13-point stars and the 27-point box, FP64 only
-// (FP32/BF16 3D grids gain from deeper blocks: the shared-memory kernel).
+// 3D: FP64 at depth 1 (the 7- and 13-point stars and the 27-point box);
+// FP32: the 7-point star at depth 2 or 3 (rs3t_kernel.cuh).
 template <class T>
-static const void* rs3_kernel_ptr(int shape, int r)
+static const void* rs3_kernel_ptr(int shape, int r, int depth)
 {
     if constexpr (sizeof(T) == 8) {
+        if (depth != 1) return nullptr;
         if (shape == kStar && r == 1) return (const void*)&rs3_kernel<T, kStar, 1>;
         if (shape == kStar && r == 2) return (const void*)&rs3_kernel<T, kStar, 2>;
         if (shape == kBox && r == 1) return (const void*)&rs3_kernel<T, kBox, 1>;
+    } else if constexpr (std::is_same<T, float>::value) {
+        if (shape == kStar && r == 1 && depth == 2) return (const void*)&rs3t_kernel<T, 2>;
+        if (shape == kStar && r == 1 && depth == 3) return (const void*)&rs3t_kernel<T, 3>;
     }
     return nullptr;
 }
 
 template <class T>
-static cudaError_t rs3_launch_t(int shape, int r, const RS3Params& p, int grid, cudaStream_t st)
+static cudaError_t rs3_launch_t(int shape, int r, int depth, const RS3Params& p, int grid, cudaStream_t st)
 {
-    const void* k = rs3_kernel_ptr<T>(shape, r);
+    const void* k = rs3_kernel_ptr<T>(shape, r, depth);
     if (!k) return cudaErrorInvalidValue;
     void* args[] = {(void*)&p};
     return cudaLaunchKernel(k, dim3(grid), dim3(kRSThreads), args, 0, st);
 }
 
 template <class T>
-static cudaError_t rs3_occupancy_t(int shape, int r, int* blocks)
+static cudaError_t rs3_occupancy_t(int shape, int r, int depth, int* blocks)
 {
-    const void* k = rs3_kernel_ptr<T>(shape, r);
+    const void* k = rs3_kernel_ptr<T>(shape, r, depth);
     if (!k) return cudaErrorInvalidValue;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, kRSThreads, 0);
 }
@@ -85,9 +90,9 @@ static cudaError_t rs3_occupancy_t(int shape, int r, int* blocks)
         return rs_launch_t<T>(s, r, d, p, g, st);                                                   \
     }                                                                                               \
     cudaError_t rs_occupancy_##NAME(int s, int r, int d, bool bt, int* b) { return rs_occupancy_t<T>(s, r, d, bt, b); } \
-    cudaError_t rs3_launch_##NAME(int s, int r, const RS3Params& p, int g, cudaStream_t st)        \
+    cudaError_t rs3_launch_##NAME(int s, int r, int d, const RS3Params& p, int g, cudaStream_t st) \
     {                                                                                               \
-        return rs3_launch_t<T>(s, r, p, g, st);                                                     \
+        return rs3_launch_t<T>(s, r, d, p, g, st);                                                  \
     }                                                                                               \
-    cudaError_t rs3_occupancy_##NAME(int s, int r, int* b) { return rs3_occupancy_t<T>(s, r, b); } \
+    cudaError_t rs3_occupancy_##NAME(int s, int r, int d, int* b) { return rs3_occupancy_t<T>(s, r, d, b); } \
     }

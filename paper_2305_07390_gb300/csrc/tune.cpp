@@ -299,16 +299,20 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
     naive.variant = 1;
     cand.push_back(naive);
     ++n;
-    // The 3D register-streaming build (FP64, depth 1): z segments sized so
+    // The 3D register-streaming build (FP64 depth 1, FP32 depths 2-3): z segments sized so
     // that one step has about 1, 2 or 4 tiles per resident warp.
     if (plan->ndim == 3 && rs3_built((int)plan->esize, plan->shape, plan->radius)) {
         const DeviceInfo& dv = device_info();
+        const int es = (int)plan->esize;
+        for (int which = 0; which < 2; ++which) {
+        const int D = rs3_depth(es, which);
+        if (which == 1 && D == rs3_depth(es, 0)) break;
         int occ = 0;
-        if (rs3_occupancy(plan, &occ) != cudaSuccess || occ < 1) {
+        if (rs3_occupancy(plan, D, &occ) != cudaSuccess || occ < 1) {
             cudaGetLastError();
         } else {
             const int64_t warps = (int64_t)occ * dv.sms * kRSWarps;
-            const int64_t S = kRS3Cols - 2LL * plan->radius, TY = rs3_rows(plan->radius);
+            const int64_t S = kRS3Cols - 2LL * D * plan->radius, TY = rs3_rows(es);
             const int64_t xy = ((plan->n[2] + S - 1) / S) * ((plan->n[1] + TY - 1) / TY);
             int64_t lastH = -1;
             for (int k : {1, 2, 4}) {
@@ -318,7 +322,7 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
                 lastH = H;
                 ebisu_params q{};
                 q.variant = 2;
-                q.depth = 1;
+                q.depth = D;
                 q.tile_s = (int32_t)H;
                 q.ctas_per_sm = occ;
                 q.threads = kRSThreads;
@@ -329,6 +333,7 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
                 cand.push_back(q);
                 ++n;
             }
+        }
         }
     }
     // The register-streaming build (2D): both built depths, segments sized so

@@ -198,7 +198,7 @@ def test_rs3_in_place_and_unsupported(steps):
     # no 3D build for the 125-point box or FP32
     p2 = eb.Plan(3, dims, 1, 2, [0.01] * 125, eb.F64, 0)
     assert p2.rs_depths() == (0, 0)
-    assert eb.Plan(3, dims, 0, 1, [0.1] * 7, eb.F32, 0).rs_depths() == (0, 0)
+    assert eb.Plan(3, dims, 1, 1, [0.03] * 27, eb.F32, 0).rs_depths() == (0, 0)
     with pytest.raises(eb.EbisuError):
         p2.set_params(variant=2, depth=1)
 
@@ -216,4 +216,57 @@ def test_rs3_wait_timeout_reports_status(monkeypatch):
     plan.run_stalled(x, y, 3, ws)
     assert plan.sync(ws) == eb.ERR_TIMEOUT
     plan.run(x, y, 3, ws)
+    assert plan.sync(ws) == 0
+
+
+# ---- 3D register streaming with temporal blocking (FP32 7-point star, depth 2, 3)
+
+@pytest.mark.parametrize("boundary", [0, 1])
+@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("steps", [1, 5, 7])
+def test_rs3t_parity(boundary, which, steps):
+    eb = _eb()
+    # ragged z segments and strips; a periodic grid's last segment, band and
+    # strip must still cover depth * radius cells
+    dims = (29, 45, 150) if boundary == 0 else (30, 44, 150)
+    g, c = synth.problem(3, dims, 0, 1, boundary, seed=420 + boundary + 3 * which)
+    x = torch.from_numpy(g).to(torch.float32).cuda()
+    held = x.double().cpu().numpy()
+    c_held = c.astype(np.float32).astype(np.float64)
+    plan = eb.Plan(3, dims, 0, 1, c, eb.F32, boundary)
+    lo, hi = plan.rs_depths()
+    assert (lo, hi) == (2, 3)
+    d = (lo, hi)[which]
+    plan.set_params(variant=2, depth=d, tile_s=9 if boundary == 0 else 10, ctas_per_sm=4)
+    p = plan.params()
+    assert (p.variant, p.tile_x, p.tile_y, p.depth) == (2, 64 - 2 * d, 4, d)
+    y = run(plan, x, steps)
+    assert torch.equal(y, run(plan, x, steps, naive=True)), "3D FP32 register-streaming and naive kernels differ"
+    ref = oracle.run(held, 0, 1, c_held, boundary, steps)
+    pad = 1 if boundary == 0 else 0
+    assert oracle.rel_linf(y.double().cpu().numpy(), ref, pad) <= TOL[1]
+    if boundary == 0:
+        m = np.ones(held.shape, bool)
+        m[1:-1, 1:-1, 1:-1] = False
+        assert np.array_equal(y.double().cpu().numpy()[m], held[m])
+
+
+def test_rs3t_in_place_and_timeout(monkeypatch):
+    eb = _eb()
+    dims = (20, 24, 90)
+    g, c = synth.problem(3, dims, 0, 1, 0, seed=430)
+    x = torch.from_numpy(g).to(torch.float32).cuda()
+    held = x.double().cpu().numpy()
+    plan = eb.Plan(3, dims, 0, 1, c, eb.F32, 0)
+    plan.set_params(variant=2, depth=3, tile_s=6, ctas_per_sm=4)
+    ws = plan.workspace()
+    y = x.clone()
+    plan.run(y, y, 4, ws)
+    assert plan.sync(ws) == 0
+    ref = oracle.run(held, 0, 1, c.astype(np.float32).astype(np.float64), 0, 4)
+    assert oracle.rel_linf(y.double().cpu().numpy(), ref, 1) <= TOL[1]
+    monkeypatch.setenv("EBISU_WAIT_TIMEOUT_MS", "200")
+    plan.run_stalled(x, y, 4, ws)
+    assert plan.sync(ws) == eb.ERR_TIMEOUT
+    plan.run(x, y, 4, ws)
     assert plan.sync(ws) == 0
