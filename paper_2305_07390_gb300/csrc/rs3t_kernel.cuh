@@ -183,18 +183,35 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, D>::minb()) rs3t_kerne
             if (per) c = (c < 0) ? c + n2 : (c >= n2 ? c - n2 : c);  // one wrap at most (n2 >= 72)
             coloff[v] = c + pad;
         }
+        // a lane's two columns as one 8-byte copy when both exist and every
+        // row starts them on an 8-byte boundary (8-byte-aligned buffer, even
+        // row pitch -- hence even plane pitch -- and even column)
+        const bool pairs = !per && colok == 3u && ((ld1 & 1) == 0) && ((coloff[0] & 1) == 0) &&
+                           ((reinterpret_cast<uintptr_t>(src) & 7) == 0);
         auto issue_plane = [&](int slot, int z) {
             T* const sp = my_stage + slot * (32 * Y0 * VX);
             if (z < hi0) {
                 const int zw = per ? ((z < 0) ? z + n0 : (z >= n0 ? z - n0 : z)) : z + pad;
                 const T* const pp = src + (int64_t)zw * lds;
+                if (pairs) {
 #pragma unroll
-                for (int i = 0; i < Y0; ++i)
-#pragma unroll
-                    for (int v = 0; v < VX; ++v) {
-                        const bool okc = ((rowok >> i) & (colok >> v)) & 1u;
-                        rs3t_cp_async<T, D>(sp + i * VX + v, okc ? pp + (rowoff[i] + coloff[v]) : src, okc ? 4 : 0);
+                    for (int i = 0; i < Y0; ++i) {
+                        const bool okr = (rowok >> i) & 1u;
+                        const unsigned sa = (unsigned)__cvta_generic_to_shared(sp + i * VX);
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa),
+                                     "l"(okr ? pp + (rowoff[i] + coloff[0]) : src), "r"(okr ? 8 : 0)
+                                     : "memory");
                     }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < Y0; ++i)
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            const bool okc = ((rowok >> i) & (colok >> v)) & 1u;
+                            rs3t_cp_async<T, D>(sp + i * VX + v, okc ? pp + (rowoff[i] + coloff[v]) : src,
+                                                okc ? 4 : 0);
+                        }
+                }
             }
             asm volatile("cp.async.commit_group;" ::: "memory");
         };
