@@ -136,19 +136,19 @@ struct RSParams {
     int32_t debug_stall;     // test hook: the first wait targets a count never reached
 };
 
-// Kernel parameters of a 3D register-streaming launch (depth 1).
+// Kernel parameters of a 3D register-streaming launch.
 struct RS3Params {
-    const void* src0;    // input of the first step
+    const void* src0;    // input of the first temporal block
     void* out;           // final destination
     void* ws;            // ping-pong buffer
     int64_t n[3];        // interior extents (z, y, x)
     int64_t lds, ld1;    // element strides of z and y
-    int64_t nitems;      // nblocks * nstrips * nbands * nsegs
+    int64_t nitems;      // nblocks * nstrips * nbands * nsegs (nbands: patches along y)
     Control* ctl;
     int64_t timeout_ns;
     int32_t pad;         // Dirichlet pad (= radius), 0 if periodic
     int32_t periodic;
-    int32_t S;           // output columns per strip (64 - 2 * radius)
+    int32_t S;           // output columns per strip (64 - 2 * depth * radius)
     int32_t H;           // output planes per z segment
     int32_t nstrips, nbands, nsegs;
     int32_t nblocks;     // ceil(steps / depth)

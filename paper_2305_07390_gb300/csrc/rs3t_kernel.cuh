@@ -56,7 +56,8 @@ struct RS3TGeom {
     }
 };
 
-template <class T, int D>
+// cp.async of one 4-byte element; src_size 0 writes zeros and reads nothing.
+template <class T>
 __device__ __forceinline__ void rs3t_cp_async(T* smem, const T* gmem, int src_size)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, D>::minb()) rs3t_kerne
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
                             const bool okc = ((rowok >> i) & (colok >> v)) & 1u;
-                            rs3t_cp_async<T, D>(sp + i * VX + v, okc ? pp + (rowoff[i] + coloff[v]) : src,
+                            rs3t_cp_async<T>(sp + i * VX + v, okc ? pp + (rowoff[i] + coloff[v]) : src,
                                                 okc ? 4 : 0);
                         }
                 }
