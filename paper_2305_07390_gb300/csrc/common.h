@@ -86,13 +86,20 @@ constexpr int rs_depth(int esize, int shape /*0 star, 1 box*/, int r, int which)
 // the rows of a warp's patch.
 constexpr bool rs3_built(int esize, int shape, int r)
 {
-    return (esize == 8 && (r == 1 || (shape == 0 && r == 2))) || (esize == 4 && shape == 0 && r == 1);
+    return (esize == 8 && (r == 1 || (shape == 0 && r == 2))) || (esize == 4 && r == 1);
 }
 // rows of a warp's patch (FP64 depth 1: 2; FP32 temporally blocked: 4)
 constexpr int rs3_rows(int esize) { return esize == 8 ? 2 : 4; }
-// temporal depths built (FP64: 1; FP32 7-point star: 2 and 3)
-constexpr int rs3_depth(int esize, int which) { return esize == 8 ? 1 : (which ? 3 : 2); }
 constexpr int kRS3Cols = 64;  // columns a warp holds (32 lanes x 2)
+// output columns per 64-column strip: the patch loses t*r columns per side;
+// the FP32 build at even depth also shifts the patch one column left so that
+// a lane's column pair starts on an even (8-byte) column
+constexpr int rs3_strip(int esize, int depth, int r)
+{
+    return kRS3Cols - 2 * depth * r - ((esize == 4 && depth % 2 == 0) ? 2 : 0);
+}
+// temporal depths built (FP64: 1; FP32: 7-point star 2 and 3, 27-point box 2)
+constexpr int rs3_depth(int esize, int shape, int which) { return esize == 8 ? 1 : ((which && shape == 0) ? 3 : 2); }
 
 // Depth the register-streaming build defaults to (FP32/BF16 storage): the
 // faster of the two built depths on 8192^2 grids (measured on GB300).

@@ -108,7 +108,7 @@ static int rs3_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L)
 {
     const int r = p->radius, es = (int)p->esize;
     if (!rs3_built(es, p->shape, r)) return EBISU_ERR_UNSUPPORTED;
-    if (q.depth != rs3_depth(es, 0) && q.depth != rs3_depth(es, 1)) return EBISU_ERR_UNSUPPORTED;
+    if (q.depth != rs3_depth(es, p->shape, 0) && q.depth != rs3_depth(es, p->shape, 1)) return EBISU_ERR_UNSUPPORTED;
     const int64_t n0 = p->n[0], n1 = p->n[1], n2 = p->n[2];
     if (n0 + 2 * p->pad > (1LL << 30) || n1 + 2 * p->pad > (1LL << 30) || n2 + 2 * p->pad > (1LL << 30))
         return EBISU_ERR_UNSUPPORTED;
@@ -116,7 +116,7 @@ static int rs3_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L)
     // the kernel wraps a periodic index at most once
     if (per && (n0 < 16 || n1 < 16 || n2 < 72)) return EBISU_ERR_UNSUPPORTED;
     const int dr = q.depth * r;
-    const int S = kRS3Cols - 2 * dr, TY = rs3_rows(es);
+    const int S = rs3_strip(es, q.depth, r), TY = rs3_rows(es);
     const int64_t H = (q.tile_s <= 0) ? n0 : std::min<int64_t>(q.tile_s, n0);
     const int64_t ns = (n2 + S - 1) / S, nb = (n1 + TY - 1) / TY, ng = (n0 + H - 1) / H;
     // a tile's inputs reach depth*r cells into its neighbours and no further
@@ -660,8 +660,8 @@ int ebisu_plan_rs_depths(ebisu_plan_t plan, int* shallow, int* deep)
     if (plan->ndim != 2) {
         const int es = (int)plan->esize;
         const bool b = rs3_built(es, plan->shape, plan->radius);
-        *shallow = b ? rs3_depth(es, 0) : 0;
-        *deep = b ? rs3_depth(es, 1) : 0;
+        *shallow = b ? rs3_depth(es, plan->shape, 0) : 0;
+        *deep = b ? rs3_depth(es, plan->shape, 1) : 0;
         return EBISU_OK;
     }
     *shallow = rs_depth((int)plan->esize, plan->shape, plan->radius, 0);

@@ -1,5 +1,6 @@
 // rs3t_kernel.cuh -- register-streaming temporally blocked kernel for 3D
-// 7-point star grids in FP32 storage (temporal depth t >= 2).
+// radius-1 grids (7-point star, 27-point box) in FP32 storage (temporal
+// depth t >= 2).
 //
 // FP32 3D stencils are memory-bound at depth 1 (the naive kernel streams at
 // the HBM rate), so they need the paper's temporal blocking (Section 4) with
@@ -15,8 +16,10 @@
 //    slot is a fixed register) and computes plane z - s when level 0
 //    receives plane z (lag 1 per level: one warp owns the whole patch, so
 //    no barrier separates the levels).
-//  * x neighbours of the centre row come from the adjacent lanes by warp
-//    shuffles; the other six neighbours are in this lane's registers.
+//  * x neighbours come from the adjacent lanes by warp shuffles: for the
+//    star only the centre row's, for the box every row of the three planes
+//    (each row shuffled once per level and step, kept while the next three
+//    output rows use it); all other neighbours are in this lane's registers.
 //  * Level-0 planes are staged 4 planes ahead in shared memory by per-lane
 //    cp.async (each lane copies and later reads back only its own cells).
 //  * Dirichlet pad cells keep their input value at every level (copied from
@@ -32,7 +35,7 @@
 
 namespace ebisu {
 
-template <class T, int D>
+template <class T, int SHAPE, int D>
 struct RS3TGeom {
     using C = typename DT<T>::C;
     static constexpr int VX = 2;   // columns per lane
@@ -47,7 +50,7 @@ struct RS3TGeom {
         return o;
     }
     static constexpr int RING = off(D);  // levels 0 .. D-1
-    static constexpr int regs() { return RING + rows(1) * VX + 80; }
+    static constexpr int regs() { return RING + rows(1) * VX + (SHAPE == kBox ? 18 : 0) + 80; }
     static constexpr int minb()
     {
         const int e = (regs() + 7) & ~7;
@@ -64,14 +67,15 @@ __device__ __forceinline__ void rs3t_cp_async(T* smem, const T* gmem, int src_si
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "r"(src_size) : "memory");
 }
 
-template <class T, int D>
-__global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, D>::minb()) rs3t_kernel(const __grid_constant__ RS3Params prm)
+template <class T, int SHAPE, int D>
+__global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
+    rs3t_kernel(const __grid_constant__ RS3Params prm)
 {
     static_assert(sizeof(T) == 4, "shared-memory staging copies 4-byte elements");
-    using G = RS3TGeom<T, D>;
+    using G = RS3TGeom<T, SHAPE, D>;
     using Dt = DT<T>;
     using C = typename Dt::C;
-    using St = Stencil<3, kStar, 1>;
+    using St = Stencil<3, SHAPE, 1>;
     constexpr int P = St::P;
     constexpr int VX = G::VX, TY = G::TY, U = G::U, PFS = G::PFS;
     constexpr int Y0 = G::rows(0);  // rows loaded per plane
@@ -148,7 +152,11 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, D>::minb()) rs3t_kerne
         const T* const src = (blk == 0) ? reinterpret_cast<const T*>(prm.src0)
                                         : reinterpret_cast<const T*>(dst_is_out ? prm.ws : prm.out);
         const int xs = strip * S, xe = min(xs + S, n2);
-        const int cb = xs - D + VX * lane;  // this lane's first column
+        // this lane's first column (even depths: the patch starts one column
+        // further left, so that with the pad of 1 a lane's pair is 8-byte
+        // aligned; the host's strip width leaves room for it)
+        constexpr int SH = (D % 2 == 0) ? 1 : 0;
+        const int cb = xs - D - SH + VX * lane;
         const int ya = band * TY;           // first output row
         const int za = seg * H, zb = min(za + H, n0);
         const int lo0 = per ? za - D : max(za - D, -pad);
@@ -244,30 +252,44 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, D>::minb()) rs3t_kerne
                     const int sn = ((u - s + 1) % U + U) % U;   // slot of plane zs + 1
                     const int ys = ya - (D - s);  // global row of level s's row 0
                     const bool copy = (s > deff) || (!per && (zs < 0 || zs >= n0));
+                    // x neighbours of level s-1 rows: WL = left lane's last
+                    // column, WR = right lane's first column, per plane
+                    // (0: zs-1, 1: zs, 2: zs+1) and row
+                    C WL[3][G::rows(0)], WR[3][G::rows(0)];
+                    auto shuffle_row = [&](int pl, int r) {
+                        const int sl = pl == 0 ? sp_ : (pl == 1 ? cs : sn);
+                        WL[pl][r] = __shfl_up_sync(FULL, Q(s - 1, sl, r, VX - 1), 1);
+                        WR[pl][r] = __shfl_down_sync(FULL, Q(s - 1, sl, r, 0), 1);
+                    };
 #pragma unroll
                     for (int i = 0; i < G::rows(s); ++i) {
                         const int ib = i + 1;  // the same row in level s-1
-                        // centre row's x neighbours
-                        const C l1 = __shfl_up_sync(FULL, Q(s - 1, cs, ib, VX - 1), 1);
-                        const C r0 = __shfl_down_sync(FULL, Q(s - 1, cs, ib, 0), 1);
+                        if constexpr (SHAPE == kBox) {
+                            // rows ib-1 .. ib+1 of all three planes; the first
+                            // two were shuffled for earlier rows
+                            if (i == 0) {
+#pragma unroll
+                                for (int pl = 0; pl < 3; ++pl) {
+                                    shuffle_row(pl, 0);
+                                    shuffle_row(pl, 1);
+                                }
+                            }
+#pragma unroll
+                            for (int pl = 0; pl < 3; ++pl) shuffle_row(pl, ib + 1);
+                        } else {
+                            shuffle_row(1, ib);  // the star: the centre row only
+                        }
                         const int y = ys + i;
                         const bool prow = !per && (y < 0 || y >= n1);
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
-                            // canonical order: (-1,0,0) (0,-1,0) (0,0,-1) (0,0,0) (0,0,1) (0,1,0) (1,0,0)
                             C acc;
 #pragma unroll
                             for (int k = 0; k < P; ++k) {
                                 const int dz = OFF.ds[k], dy = OFF.d1[k], dx = OFF.d2[k];
-                                C val;
-                                if (dz != 0) {
-                                    val = Q(s - 1, dz < 0 ? sp_ : sn, ib, v);
-                                } else if (dy != 0) {
-                                    val = Q(s - 1, cs, ib + dy, v);
-                                } else {
-                                    const int cx = v + dx;
-                                    val = (cx < 0) ? l1 : (cx >= VX ? r0 : Q(s - 1, cs, ib, cx));
-                                }
+                                const int pl = dz + 1, r = ib + dy, cx = v + dx;
+                                const int sl = pl == 0 ? sp_ : (pl == 1 ? cs : sn);
+                                const C val = (cx < 0) ? WL[pl][r] : (cx >= VX ? WR[pl][r] : Q(s - 1, sl, r, cx));
                                 const C ck = prm.coef_f[k];
                                 acc = (k == 0) ? Dt::mul(ck, val) : Dt::fma(ck, val, acc);
                             }

@@ -48,7 +48,7 @@ static cudaError_t rs_occupancy_t(int shape, int r, int depth, bool batch, int* 
 }
 
 // 3D: FP64 at depth 1 (the 7- and 13-point stars and the 27-point box);
-// FP32: the 7-point star at depth 2 or 3 (rs3t_kernel.cuh).
+// FP32: the 7-point star at depth 2 or 3, the 27-point box at depth 2 (rs3t_kernel.cuh).
 template <class T>
 static const void* rs3_kernel_ptr(int shape, int r, int depth)
 {
@@ -58,8 +58,9 @@ static const void* rs3_kernel_ptr(int shape, int r, int depth)
         if (shape == kStar && r == 2) return (const void*)&rs3_kernel<T, kStar, 2>;
         if (shape == kBox && r == 1) return (const void*)&rs3_kernel<T, kBox, 1>;
     } else if constexpr (std::is_same<T, float>::value) {
-        if (shape == kStar && r == 1 && depth == 2) return (const void*)&rs3t_kernel<T, 2>;
-        if (shape == kStar && r == 1 && depth == 3) return (const void*)&rs3t_kernel<T, 3>;
+        if (r == 1 && shape == kStar && depth == 2) return (const void*)&rs3t_kernel<T, kStar, 2>;
+        if (r == 1 && shape == kStar && depth == 3) return (const void*)&rs3t_kernel<T, kStar, 3>;
+        if (r == 1 && shape == kBox && depth == 2) return (const void*)&rs3t_kernel<T, kBox, 2>;
     }
     return nullptr;
 }

@@ -305,14 +305,14 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
         const DeviceInfo& dv = device_info();
         const int es = (int)plan->esize;
         for (int which = 0; which < 2; ++which) {
-        const int D = rs3_depth(es, which);
-        if (which == 1 && D == rs3_depth(es, 0)) break;
+        const int D = rs3_depth(es, plan->shape, which);
+        if (which == 1 && D == rs3_depth(es, plan->shape, 0)) break;
         int occ = 0;
         if (rs3_occupancy(plan, D, &occ) != cudaSuccess || occ < 1) {
             cudaGetLastError();
         } else {
             const int64_t warps = (int64_t)occ * dv.sms * kRSWarps;
-            const int64_t S = kRS3Cols - 2LL * D * plan->radius, TY = rs3_rows(es);
+            const int64_t S = rs3_strip(es, D, plan->radius), TY = rs3_rows(es);
             const int64_t xy = ((plan->n[2] + S - 1) / S) * ((plan->n[1] + TY - 1) / TY);
             int64_t lastH = -1;
             for (int k : {1, 2, 4}) {

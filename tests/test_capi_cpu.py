@@ -107,15 +107,16 @@ def test_register_streaming_params():
         big.set_params(variant=2, depth=lo, tile_s=lo)
     assert ei.value.code == ebisu.ERR_UNSUPPORTED
     # no 3D build; periodic grids must be at least 64 x 136
-    # 3D FP32: the 7-point star at depths 2 and 3 (64 - 2t column strips of
-    # 4-row patches); no other FP32/BF16 3D stencil
+    # 3D FP32: the 7-point star at depths 2 and 3, the 27-point box at depth 2
+    # (64 - 2t column strips of 4-row patches); no BF16 3D build
     p3 = ebisu.Plan(3, (20, 20, 80), 0, 1, [0.1] * 7, ebisu.F32, ebisu.DIRICHLET)
     assert p3.rs_depths() == (2, 3)
     p3.set_params(variant=2, depth=3, tile_s=5)
     assert (p3.params().tile_x, p3.params().tile_y) == (58, 4)
     with pytest.raises(ebisu.EbisuError):
         p3.set_params(variant=2, depth=4)
-    assert ebisu.Plan(3, (20, 20, 20), 1, 1, [0.03] * 27, ebisu.F32, ebisu.DIRICHLET).rs_depths() == (0, 0)
+    assert ebisu.Plan(3, (20, 20, 20), 1, 1, [0.03] * 27, ebisu.F32, ebisu.DIRICHLET).rs_depths() == (2, 2)
+    assert ebisu.Plan(3, (20, 20, 20), 0, 2, [0.07] * 13, ebisu.F32, ebisu.DIRICHLET).rs_depths() == (0, 0)
     assert ebisu.Plan(3, (20, 20, 20), 0, 1, [0.1] * 7, ebisu.BF16, ebisu.DIRICHLET).rs_depths() == (0, 0)
     # 3D: FP64 radius 1 only, depth 1, 62-column strips of 2-row patches
     p3d = ebisu.Plan(3, (64, 64, 200), 1, 1, [0.03] * 27, ebisu.F64, ebisu.DIRICHLET)
