@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
     Control* const ctl = prm.ctl;
     // coefficients: in the parameter bank for a single problem (FMAs take
     // them as operands), in registers (loaded per item) for a batch
-    C cr[BATCH ? P : 1];
+    C cr[BATCH ? P : 1] = {};
     auto coef = [&](int k) -> C {
         if constexpr (BATCH) return cr[k];
         else if constexpr (sizeof(C) == 8) return prm.g.coef[k];
