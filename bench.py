@@ -317,6 +317,64 @@ def run_paper_sizes(args):
                       "rows": rows}), flush=True)
 
 
+def run_ablation(args):
+    """What each element of the design buys on this GPU, for the 2D 5-point
+    and 25-point stencils (8192^2) and the 3D 7-point star (512^3), FP32 and
+    FP64: the naive one-step kernel (no on-chip reuse); the shared-memory
+    kernel at depth 1 (tiles and prefetched plane rings, no temporal reuse);
+    the shared-memory kernel at depth 4 (plus temporal blocking with lazy
+    streaming, one barrier per plane); the register-streaming kernel at its
+    shallow and deep depth (queues in registers, no barrier).  Steps: 96
+    (2D) / 24 (3D); rows print as they finish."""
+    import torch
+    from paper_2305_07390_gb300 import ebisu, synth
+    stream = torch.cuda.current_stream()
+    sh = ebisu.current_stream_handle()
+    rows = []
+    cases = [("j2d5pt", 2, (8192, 8192), 0, 1, 96, dict(tile_x=1024, tile_s=108)),
+             ("j2d25pt", 2, (8192, 8192), 1, 2, 96, dict(tile_x=512, tile_s=108)),
+             ("j3d7pt", 3, (512, 512, 512), 0, 1, 24, dict(tile_x=64, tile_y=32, tile_s=103))]
+    for name, nd, dims, shape, r, steps, tb in cases:
+        g, c = synth.problem(nd, dims, shape, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED)
+        cells = 1
+        for d_ in dims:
+            cells *= d_
+        for dname, dt in (("f32", ebisu.F32), ("f64", ebisu.F64)):
+            plan = ebisu.Plan(nd, dims, shape, r, c, dt, ebisu.DIRICHLET)
+            x = torch.from_numpy(g).to(ebisu.torch_dtype(dt)).cuda()
+            y = torch.empty_like(x)
+            ws = plan.workspace()
+            lo, hi = plan.rs_depths()
+            variants = [("naive one-step kernel", None, True),
+                        ("shared memory, depth 1", dict(tb, depth=1, ctas_per_sm=2), False),
+                        ("shared memory, depth 4", dict(tb, depth=4, ctas_per_sm=2), False)]
+            for d in sorted({lo, hi} - {0}):
+                variants.append((f"register streaming, depth {d}",
+                                 dict(variant=2, depth=d, tile_s=128, ctas_per_sm=8), False))
+            for label, params, naive in variants:
+                try:
+                    if params is not None:
+                        plan.set_params(**params)
+                except ebisu.EbisuError:
+                    continue
+                plan.run(x, y, steps, ws, stream=sh, naive=naive)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                plan.run(x, y, steps, ws, stream=sh, naive=naive)
+                b.record(stream)
+                b.synchronize()
+                rc = plan.sync(ws)
+                if rc != 0:
+                    continue
+                rate = cells * steps / (a.elapsed_time(b) * 1e-3)
+                rows.append({"stencil": name, "dtype": dname, "variant": label, "cell_updates_per_s": rate})
+                print(json.dumps(rows[-1]), flush=True)
+            del x, y, ws, plan
+            torch.cuda.empty_cache()
+    print(json.dumps({"workload": "ablation of the design's elements (naive, shared-memory depth 1 and 4, "
+                                  "register streaming)", "rows": rows}), flush=True)
+
+
 def npoints3(shape, r):
     return 6 * r + 1 if shape == 0 else (2 * r + 1) ** 3
 
@@ -329,8 +387,9 @@ def run_batch(args):
     import torch
     from paper_2305_07390_gb300 import ebisu, synth
     mix = synth.batch_mix(512)
-    out = {"workload": "batch: 512 uneven 2D 9-point box grids, Dirichlet, tiles and depth from the autotuner's "
-                       "cost model", "n_grids": len(mix), "cells": int(sum(a * b for a, b, _ in mix)),
+    out = {"workload": "batch: 512 uneven 2D 9-point box grids, Dirichlet; each plan's default parameters (FP64: "
+                       "the cost model's shared-memory tiles and depth; FP32/BF16: the register-streaming build "
+                       "at its preferred depth)", "n_grids": len(mix), "cells": int(sum(a * b for a, b, _ in mix)),
            "cell_updates": int(sum(a * b * s for a, b, s in mix)), "by_dtype": {}}
     stream = torch.cuda.current_stream()
     for dname, dt in (("f64", ebisu.F64), ("f32", ebisu.F32), ("bf16", ebisu.BF16)):
@@ -477,11 +536,11 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="--case: storage type")
     ap.add_argument("--params", default="", help="--case: plan parameters, k=v,k=v")
     ap.add_argument("--naive", action="store_true", help="--case: the one-step-per-launch kernel")
-    ap.add_argument("--workload", default="set", choices=["set", "set3d", "batch", "serve", "paper"],
+    ap.add_argument("--workload", default="set", choices=["set", "set3d", "batch", "serve", "paper", "ablation"],
                     help="set: the FP64 2D stencil set (default, the headline line); set3d: the FP64 3D "
                          "set; batch: 512 uneven 2D 9-point box grids in one persistent launch per dtype; "
                          "serve: Poisson arrivals through the serving loop; paper: the paper's stencils at "
-                         "its domain sizes")
+                         "its domain sizes; ablation: what each design element buys")
     ap.add_argument("--serve-rates", default="5,10,20,50,100,200,500,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
@@ -493,6 +552,8 @@ def main():
         return run_set3d(args)
     if args.workload == "paper":
         return run_paper_sizes(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
     if args.workload == "serve":
         return run_serve(args)
     if args.warmup < 3:
