@@ -36,6 +36,16 @@ struct PadParams {
     cudaError_t reduce_partial_##NAME(const void* a, const void* b, double* part,                \
                                       const PadParams& p, int64_t* n, cudaStream_t st);
 
+// kernel lookups of the register-streaming builds (see rs_impl.cuh)
+#define EBISU_DECLARE_RS_PTRS(NAME)                                \
+    const void* rs_ptr_##NAME##_0(int shape, int r, int depth);    \
+    const void* rs_ptr_##NAME##_1(int shape, int r, int depth);    \
+    const void* rs3_ptr_##NAME(int shape, int r, int depth);
+
+EBISU_DECLARE_RS_PTRS(f64)
+EBISU_DECLARE_RS_PTRS(f32)
+EBISU_DECLARE_RS_PTRS(bf16)
+
 #define EBISU_DECLARE_RS_ENTRY(NAME)                                                               \
     cudaError_t rs_launch_##NAME(int s, int r, int d, const RSParams& p, int g, cudaStream_t st);   \
     cudaError_t rs_occupancy_##NAME(int s, int r, int d, bool batch, int* b);                      \

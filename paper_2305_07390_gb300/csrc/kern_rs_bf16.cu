@@ -1,3 +1,3 @@
-// Register-streaming kernel instantiations (2D) for BF16 storage (FP32 arithmetic).
+// Register-streaming kernels for BF16 storage (FP32 arithmetic): launchers.
 #include "rs_impl.cuh"
 EBISU_DEFINE_RS_ENTRY(__nv_bfloat16, bf16)

@@ -1,3 +1,3 @@
-// Register-streaming kernel instantiations (2D) for FP32 storage.
+// Register-streaming kernels for FP32 storage: launchers.
 #include "rs_impl.cuh"
 EBISU_DEFINE_RS_ENTRY(float, f32)

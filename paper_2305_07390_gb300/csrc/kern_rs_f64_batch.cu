@@ -1,0 +1,4 @@
+// Register-streaming 2D kernels for FP64 storage, batched launches.
+#define EBISU_RS2D_KERNELS
+#include "rs_impl.cuh"
+EBISU_DEFINE_RS2D_PTRS(double, f64, 1)
