@@ -38,6 +38,12 @@
 
 namespace ebisu {
 
+// packed two-cell FP32 FMAs (sm_100 family) in the register-streaming kernel
+#ifndef EBISU_RS_PACKED_FMA
+#define EBISU_RS_PACKED_FMA 1
+#endif
+constexpr bool kRSPackedFma = EBISU_RS_PACKED_FMA != 0;
+
 template <class T, int SHAPE, int R>
 struct RSGeom {
     using C = typename DT<T>::C;
@@ -343,6 +349,7 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
         // the short tails form a chain through the levels.
         // (star: the centre row's r edge cells come from the adjacent lanes)
         constexpr int kTail = P - (EXT ? 2 * R + 1 : 1);  // first term on row +r
+        constexpr bool kPair = (sizeof(C) == 4) && !EXT && kRSPackedFma;
         // The accumulators of levels below t are the queue slots they fill
         // (the slot's old row is dead by then), so no copy follows the FMAs.
         C accD[4];  // level t's row (to global memory)
@@ -366,6 +373,31 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                 const int dy = OFF.ds[k], dx = OFF.d2[k];
                 const int rs = (cs + dy + U) % U;
                 const C ck = coef(k);
+                // FP32 arithmetic, star: where a term's four values are the
+                // two register pairs of a queued row (dx even), two cells per
+                // packed FMA (per-element round to nearest: the same result
+                // as two scalar FMAs)
+                if constexpr (kPair) {
+                    if ((dx & 1) == 0) {
+                        const float2 ck2 = make_float2(ck, ck);
+#pragma unroll
+                        for (int q2 = 0; q2 < 2; ++q2) {
+                            C v[2];
+#pragma unroll
+                            for (int w = 0; w < 2; ++w) {
+                                const int m = 2 * q2 + w;
+                                v[w] = (dy == 0) ? e[R + m + dx] : ring[s - 1][rs][m];
+                            }
+                            C& a0 = acc_ref(s, cs, 2 * q2);
+                            C& a1 = acc_ref(s, cs, 2 * q2 + 1);
+                            const float2 r2 = (k == 0) ? __fmul2_rn(ck2, make_float2(v[0], v[1]))
+                                                       : __ffma2_rn(ck2, make_float2(v[0], v[1]), make_float2(a0, a1));
+                            a0 = r2.x;
+                            a1 = r2.y;
+                        }
+                        continue;
+                    }
+                }
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     C v;
