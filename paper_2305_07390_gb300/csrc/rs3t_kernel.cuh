@@ -35,6 +35,12 @@
 
 namespace ebisu {
 
+// packed two-cell FP32 FMAs (sm_100 family) for the terms without an x offset
+#ifndef EBISU_RS3T_PACKED_FMA
+#define EBISU_RS3T_PACKED_FMA 1
+#endif
+constexpr bool kRS3TPackedFma = EBISU_RS3T_PACKED_FMA != 0;
+
 template <class T, int SHAPE, int D>
 struct RS3TGeom {
     using C = typename DT<T>::C;
@@ -281,20 +287,36 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
                         }
                         const int y = ys + i;
                         const bool prow = !per && (y < 0 || y >= n1);
+                        C acc[VX];
+#pragma unroll
+                        for (int k = 0; k < P; ++k) {
+                            const int dz = OFF.ds[k], dy = OFF.d1[k], dx = OFF.d2[k];
+                            const int pl = dz + 1, r = ib + dy;
+                            const int sl = pl == 0 ? sp_ : (pl == 1 ? cs : sn);
+                            const C ck = prm.coef_f[k];
+                            // dx = 0: the lane's pair is one register pair --
+                            // both cells in one packed FMA (per-element round
+                            // to nearest, the same result as two scalar FMAs)
+                            if (kRS3TPackedFma && dx == 0) {
+                                const float2 c2 = make_float2(ck, ck);
+                                const float2 v2 = make_float2(Q(s - 1, sl, r, 0), Q(s - 1, sl, r, 1));
+                                const float2 r2 = (k == 0) ? __fmul2_rn(c2, v2)
+                                                           : __ffma2_rn(c2, v2, make_float2(acc[0], acc[1]));
+                                acc[0] = r2.x;
+                                acc[1] = r2.y;
+                                continue;
+                            }
+#pragma unroll
+                            for (int v = 0; v < VX; ++v) {
+                                const int cx = v + dx;
+                                const C val = (cx < 0) ? WL[pl][r] : (cx >= VX ? WR[pl][r] : Q(s - 1, sl, r, cx));
+                                acc[v] = (k == 0) ? Dt::mul(ck, val) : Dt::fma(ck, val, acc[v]);
+                            }
+                        }
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
-                            C acc;
-#pragma unroll
-                            for (int k = 0; k < P; ++k) {
-                                const int dz = OFF.ds[k], dy = OFF.d1[k], dx = OFF.d2[k];
-                                const int pl = dz + 1, r = ib + dy, cx = v + dx;
-                                const int sl = pl == 0 ? sp_ : (pl == 1 ? cs : sn);
-                                const C val = (cx < 0) ? WL[pl][r] : (cx >= VX ? WR[pl][r] : Q(s - 1, sl, r, cx));
-                                const C ck = prm.coef_f[k];
-                                acc = (k == 0) ? Dt::mul(ck, val) : Dt::fma(ck, val, acc);
-                            }
                             const bool keep = copy || prow || ((padc >> v) & 1u);
-                            const C o = keep ? Q(s - 1, cs, ib, v) : Dt::widen(Dt::narrow(acc));
+                            const C o = keep ? Q(s - 1, cs, ib, v) : Dt::widen(Dt::narrow(acc[v]));
                             if (s < D) {
                                 Q(s < D ? s : 0, cs, i, v) = o;
                             } else if (zs >= za && zs < zb && i < TY && ya + i < n1 && ((outc >> v) & 1u)) {

@@ -349,7 +349,13 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
         // the short tails form a chain through the levels.
         // (star: the centre row's r edge cells come from the adjacent lanes)
         constexpr int kTail = P - (EXT ? 2 * R + 1 : 1);  // first term on row +r
-        constexpr bool kPair = (sizeof(C) == 4) && !EXT && kRSPackedFma;
+        // box stencils: only while the ring is shallow (t*r <= 4); at depth 6
+        // the register pairs the packed form needs cost more than the halved
+        // FMA count (measured: 9-point box t = 6 -6%, 25-point box t = 2 +9%)
+        // (BF16 storage, 13-point star: the packed form spills under the
+        // register cap, so it keeps scalar FMAs)
+        constexpr bool kPair = (sizeof(C) == 4) && kRSPackedFma && (!EXT || D * R <= 4) &&
+                               !(sizeof(T) == 2 && !EXT && R == 3);
         // The accumulators of levels below t are the queue slots they fill
         // (the slot's old row is dead by then), so no copy follows the FMAs.
         C accD[4];  // level t's row (to global memory)
@@ -373,12 +379,12 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                 const int dy = OFF.ds[k], dx = OFF.d2[k];
                 const int rs = (cs + dy + U) % U;
                 const C ck = coef(k);
-                // FP32 arithmetic, star: where a term's four values are the
-                // two register pairs of a queued row (dx even), two cells per
-                // packed FMA (per-element round to nearest: the same result
-                // as two scalar FMAs)
+                // FP32 arithmetic: where a term's four values are two
+                // register pairs of a queued row (star: dx even), two cells
+                // per packed FMA (per-element round to nearest: the same
+                // result as two scalar FMAs)
                 if constexpr (kPair) {
-                    if ((dx & 1) == 0) {
+                    if (((EXT ? X0 + dx : dx) & 1) == 0) {
                         const float2 ck2 = make_float2(ck, ck);
 #pragma unroll
                         for (int q2 = 0; q2 < 2; ++q2) {
@@ -386,7 +392,8 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
 #pragma unroll
                             for (int w = 0; w < 2; ++w) {
                                 const int m = 2 * q2 + w;
-                                v[w] = (dy == 0) ? e[R + m + dx] : ring[s - 1][rs][m];
+                                v[w] = EXT ? ring[s - 1][rs][X0 + m + dx]
+                                           : ((dy == 0) ? e[R + m + dx] : ring[s - 1][rs][m]);
                             }
                             C& a0 = acc_ref(s, cs, 2 * q2);
                             C& a1 = acc_ref(s, cs, 2 * q2 + 1);
