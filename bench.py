@@ -68,6 +68,16 @@ VARIANT_NAMES = {0: "fused (shared-memory queues)", 1: "naive", 2: "fused (regis
 KERNEL_NAMES = {0: "tb_kernel", 1: "naive_kernel", 2: "rs_kernel"}
 
 
+def kernel_name(plan):
+    """The kernel a plan's current parameters launch (3D register streaming:
+    the depth-1 FP64 build or the temporally blocked FP32 build)."""
+    from paper_2305_07390_gb300 import ebisu
+    v = plan.params().variant
+    if v == 2 and plan.ndim == 3:
+        return "rs3_kernel" if plan.dtype == ebisu.F64 else "rs3t_kernel"
+    return KERNEL_NAMES[v]
+
+
 def npoints(shape, r):
     return 4 * r + 1 if shape == 0 else (2 * r + 1) ** 2
 
@@ -250,7 +260,7 @@ def run_set3d(args):
         rows.append({"stencil": name, "points": P, "ms": ms, "cell_updates_per_s": rate,
                      "roofline_frac": rate * 2 * P / FP64_PEAK_FLOPS,
                      "naive_cell_updates_per_s": n ** 3 * ns / (ms_naive * 1e-3),
-                     "tuner_preferred": VARIANT_NAMES[pref],
+                     "tuner_preferred": VARIANT_NAMES[pref], "kernel": kernel_name(plan),
                      "params": plan.params().as_dict()})
         print(json.dumps(rows[-1]), flush=True)
         del x, y, ws, plan
@@ -308,7 +318,7 @@ def run_paper_sizes(args):
             rows.append({"stencil": name, "dtype": dname, "dims": list(dims), "steps": steps, "points": P,
                          "cell_updates_per_s": rate, "tflops": rate * 2 * P / 1e12,
                          "naive_cell_updates_per_s": cells * ns / (a.elapsed_time(b) * 1e-3),
-                         "tuner_preferred": VARIANT_NAMES[pref], "kernel": KERNEL_NAMES[plan.params().variant],
+                         "tuner_preferred": VARIANT_NAMES[pref], "kernel": kernel_name(plan),
                          "params": plan.params().as_dict()})
             print(json.dumps(rows[-1]), flush=True)
             del x, y, ws, plan
@@ -663,7 +673,7 @@ def main():
         d["naive_cell_updates_per_s"] = cells * nsteps / (a.elapsed_time(b) * 1e-3)
         d["speedup_vs_naive"] = d["cell_updates_per_s"] / d["naive_cell_updates_per_s"]
         d["tuner_preferred"] = VARIANT_NAMES[p["tuned_variant"]]
-        d["kernel"] = KERNEL_NAMES[p["plan"].params().variant]
+        d["kernel"] = kernel_name(p["plan"])
     dom = max(per, key=lambda d: d["ms_per_launch"])
     achieved = dom["tflops"]
     dom_name = f"{dom['kernel']}<double,2D,{dom['stencil']}>"
@@ -727,7 +737,7 @@ def main():
                              speedup_vs_fp64=rate / d["cell_updates_per_s"],
                              naive_cell_updates_per_s=naive_rate, speedup_vs_naive=rate / naive_rate,
                              rel_linf_vs_fp64=err, tuner_preferred=VARIANT_NAMES[tuned],
-                             kernel=KERNEL_NAMES[plan.params().variant], params=plan.params().as_dict()))
+                             kernel=kernel_name(plan), params=plan.params().as_dict()))
             del xl, yl, wsl, plan
         torch.cuda.empty_cache()
         forms.append(dict(dtype=dname, per_stencil=rows,
