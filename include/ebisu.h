@@ -85,13 +85,13 @@ enum ebisu_boundary { EBISU_DIRICHLET = 0, EBISU_PERIODIC = 1 };
  *                    128-column strip, every time level in registers; in 3D
  *                    one warp per 64-column patch streamed along z (FP64,
  *                    radius 1 and the 13-point star: 2 rows, depth 1; FP32
- *                    radius 1: 4 rows, depth 2 or 3 for the star, 2 for the
- *                    box).  depth
+ *                    and BF16 radius 1: 4 rows, depth 2 or 3 for the star,
+ *                    2 for the box).  depth
  *                    must be one of ebisu_plan_rs_depths(), tile_s is the
  *                    rows (2D) or planes (3D) per segment, ctas_per_sm caps
  *                    the resident 128-thread CTAs, and tile_x / tile_y are
  *                    set to the strip's output width (128 - 2*depth*radius;
- *                    3D: 64 - 2*depth*radius, 2 fewer for FP32 at even
+ *                    3D: 64 - 2*depth*radius, 2 fewer for FP32/BF16 at even
  *                    depth) and the patch's rows.  Batches run
  *                    2D variant-2 plans with the register-streaming kernel
  *                    and every other plan with variant 0, using the last
@@ -155,7 +155,8 @@ int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* p);
  * this plan's stencil and storage type (Section 4's temporal blocking with
  * the per-level queues held in registers): *shallow <= *deep.  3D plans: 1
  * and 1 for the FP64 7- and 13-point stars and 27-point box, 2 and 3 for
- * the FP32 7-point star, 2 and 2 for the FP32 27-point box, else 0 and 0
+ * the FP32 and BF16 7-point stars, 2 and 2 for the FP32 and BF16 27-point
+ * boxes, else 0 and 0
  * (no such kernel).  Host only; never
  * fails for a valid plan. */
 int ebisu_plan_rs_depths(ebisu_plan_t plan, int* shallow, int* deep);

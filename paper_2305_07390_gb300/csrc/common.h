@@ -82,23 +82,25 @@ constexpr int rs_depth(int esize, int shape /*0 star, 1 box*/, int r, int which)
     return r == 1 ? (which ? 6 : 3) : (which ? 2 : 1);
 }
 
-// 3D register-streaming build (depth 1, FP64): which stencils it covers and
-// the rows of a warp's patch.
+// 3D register-streaming builds: which stencils they cover (FP64 at depth 1:
+// the 7- and 13-point stars and the 27-point box; FP32 and BF16 temporally
+// blocked: radius 1) and the rows of a warp's patch.
 constexpr bool rs3_built(int esize, int shape, int r)
 {
-    return (esize == 8 && (r == 1 || (shape == 0 && r == 2))) || (esize == 4 && r == 1);
+    return (esize == 8 && (r == 1 || (shape == 0 && r == 2))) || (esize != 8 && r == 1);
 }
-// rows of a warp's patch (FP64 depth 1: 2; FP32 temporally blocked: 4)
+// rows of a warp's patch (FP64 depth 1: 2; FP32/BF16 temporally blocked: 4)
 constexpr int rs3_rows(int esize) { return esize == 8 ? 2 : 4; }
 constexpr int kRS3Cols = 64;  // columns a warp holds (32 lanes x 2)
 // output columns per 64-column strip: the patch loses t*r columns per side;
-// the FP32 build at even depth also shifts the patch one column left so that
-// a lane's column pair starts on an even (8-byte) column
+// the FP32/BF16 build at even depth also shifts the patch one column left so
+// that a lane's column pair starts on an even column
 constexpr int rs3_strip(int esize, int depth, int r)
 {
-    return kRS3Cols - 2 * depth * r - ((esize == 4 && depth % 2 == 0) ? 2 : 0);
+    return kRS3Cols - 2 * depth * r - ((esize != 8 && depth % 2 == 0) ? 2 : 0);
 }
-// temporal depths built (FP64: 1; FP32: 7-point star 2 and 3, 27-point box 2)
+// temporal depths built (FP64: 1; FP32/BF16: 7-point star 2 and 3, 27-point
+// box 2)
 constexpr int rs3_depth(int esize, int shape, int which) { return esize == 8 ? 1 : ((which && shape == 0) ? 3 : 2); }
 
 // Depth the register-streaming build defaults to (FP32/BF16 storage): the

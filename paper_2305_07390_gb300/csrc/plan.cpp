@@ -125,7 +125,7 @@ static int rs3_layout(const ebisu_plan_s* p, const ebisu_params& q, RSLayout* L)
                 (ng > 1 && n0 - (ng - 1) * H < dr)))
         return EBISU_ERR_UNSUPPORTED;
     if (ns * nb * ng > kRSMaxTiles) return EBISU_ERR_UNSUPPORTED;
-    // the FP32 build addresses within a plane with 32-bit offsets
+    // the FP32/BF16 build addresses within a plane with 32-bit offsets
     if ((n1 + 2 * p->pad) * (n2 + 2 * p->pad) >= (1LL << 31)) return EBISU_ERR_UNSUPPORTED;
     if (L) {
         L->S = S;
@@ -321,6 +321,7 @@ cudaError_t rs3_launch(const ebisu_plan_s* p, int depth, const RS3Params& prm, i
     switch (p->dtype) {
     case EBISU_F64: return rs3_launch_f64(p->shape, p->radius, depth, prm, grid, st);
     case EBISU_F32: return rs3_launch_f32(p->shape, p->radius, depth, prm, grid, st);
+    case EBISU_BF16: return rs3_launch_bf16(p->shape, p->radius, depth, prm, grid, st);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -330,6 +331,7 @@ cudaError_t rs3_occupancy(const ebisu_plan_s* p, int depth, int* blocks)
     switch (p->dtype) {
     case EBISU_F64: return rs3_occupancy_f64(p->shape, p->radius, depth, blocks);
     case EBISU_F32: return rs3_occupancy_f32(p->shape, p->radius, depth, blocks);
+    case EBISU_BF16: return rs3_occupancy_bf16(p->shape, p->radius, depth, blocks);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -378,7 +380,7 @@ int64_t fill_rs_grid(const ebisu_plan_s* p, const RSLayout& L, const void* in, v
     return nb;
 }
 
-// A run of the 3D register-streaming build (FP64: depth 1; FP32: depth 2 or
+// A run of the 3D register-streaming build (FP64: depth 1; FP32/BF16: depth 2 or
 // 3).  The kernel never writes pad cells: the buffers it writes first get the
 // input's pad from a copy kernel.
 static int run_rs3(ebisu_plan_t p, const void* in, void* out, int64_t steps, void* ws, cudaStream_t st,

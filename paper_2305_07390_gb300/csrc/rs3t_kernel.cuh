@@ -1,6 +1,6 @@
 // rs3t_kernel.cuh -- register-streaming temporally blocked kernel for 3D
-// radius-1 grids (7-point star, 27-point box) in FP32 storage (temporal
-// depth t >= 2).
+// radius-1 grids (7-point star, 27-point box) in FP32 or BF16 storage with
+// FP32 arithmetic (temporal depth t >= 2).
 //
 // FP32 3D stencils are memory-bound at depth 1 (the naive kernel streams at
 // the HBM rate), so they need the paper's temporal blocking (Section 4) with
@@ -77,7 +77,7 @@ template <class T, int SHAPE, int D>
 __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
     rs3t_kernel(const __grid_constant__ RS3Params prm)
 {
-    static_assert(sizeof(T) == 4, "shared-memory staging copies 4-byte elements");
+    static_assert(sizeof(T) == 4 || sizeof(T) == 2, "FP32 or BF16 storage");
     using G = RS3TGeom<T, SHAPE, D>;
     using Dt = DT<T>;
     using C = typename Dt::C;
@@ -198,11 +198,12 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
             if (per) c = (c < 0) ? c + n2 : (c >= n2 ? c - n2 : c);  // one wrap at most (n2 >= 72)
             coloff[v] = c + pad;
         }
-        // a lane's two columns as one 8-byte copy when both exist and every
-        // row starts them on an 8-byte boundary (8-byte-aligned buffer, even
-        // row pitch -- hence even plane pitch -- and even column)
+        // a lane's two columns as one copy (8 bytes FP32, 4 bytes BF16) when
+        // both exist and every row starts them on a pair boundary (aligned
+        // buffer, even row pitch -- hence even plane pitch -- and even column)
+        constexpr int PB = 2 * (int)sizeof(T);  // bytes of a lane's column pair
         const bool pairs = !per && colok == 3u && ((ld1 & 1) == 0) && ((coloff[0] & 1) == 0) &&
-                           ((reinterpret_cast<uintptr_t>(src) & 7) == 0);
+                           ((reinterpret_cast<uintptr_t>(src) & (PB - 1)) == 0);
         auto issue_plane = [&](int slot, int z) {
             T* const sp = my_stage + slot * (32 * Y0 * VX);
             if (z < hi0) {
@@ -213,10 +214,22 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
                     for (int i = 0; i < Y0; ++i) {
                         const bool okr = (rowok >> i) & 1u;
                         const unsigned sa = (unsigned)__cvta_generic_to_shared(sp + i * VX);
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(sa),
-                                     "l"(okr ? pp + (rowoff[i] + coloff[0]) : src), "r"(okr ? 8 : 0)
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(sa),
+                                     "l"(okr ? pp + (rowoff[i] + coloff[0]) : src), "n"(PB), "r"(okr ? PB : 0)
                                      : "memory");
                     }
+                } else if constexpr (sizeof(T) == 2) {
+                    // 2-byte cells have no cp.async form: plain loads into the
+                    // lane's own slots (read back only by this thread)
+                    unsigned short* const sp16 = reinterpret_cast<unsigned short*>(sp);
+                    const unsigned short* const pp16 = reinterpret_cast<const unsigned short*>(pp);
+#pragma unroll
+                    for (int i = 0; i < Y0; ++i)
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            const bool okc = ((rowok >> i) & (colok >> v)) & 1u;
+                            sp16[i * VX + v] = okc ? __ldg(pp16 + (rowoff[i] + coloff[v])) : (unsigned short)0;
+                        }
                 } else {
 #pragma unroll
                     for (int i = 0; i < Y0; ++i)

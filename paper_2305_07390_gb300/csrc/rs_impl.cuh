@@ -55,8 +55,8 @@ static const void* rs_ptr_pick(int depth)
 #include "rs3_kernel.cuh"
 #include "rs3t_kernel.cuh"
 // defines rs3_ptr_<NAME>(shape, r, depth): FP64 at depth 1 (the 7- and
-// 13-point stars and the 27-point box); FP32 radius 1: the 7-point star at
-// depth 2 or 3, the 27-point box at depth 2
+// 13-point stars and the 27-point box); FP32 and BF16 radius 1: the 7-point
+// star at depth 2 or 3, the 27-point box at depth 2
 #define EBISU_DEFINE_RS3D_PTRS(T, NAME)                                                                \
     namespace ebisu {                                                                                  \
     const void* rs3_ptr_##NAME(int shape, int r, int depth)                                            \
@@ -66,7 +66,7 @@ static const void* rs_ptr_pick(int depth)
             if (shape == kStar && r == 1) return (const void*)&rs3_kernel<T, kStar, 1>;                \
             if (shape == kStar && r == 2) return (const void*)&rs3_kernel<T, kStar, 2>;                \
             if (shape == kBox && r == 1) return (const void*)&rs3_kernel<T, kBox, 1>;                  \
-        } else if constexpr (std::is_same<T, float>::value) {                                          \
+        } else {                                                                                       \
             if (r == 1 && shape == kStar && depth == 2) return (const void*)&rs3t_kernel<T, kStar, 2>; \
             if (r == 1 && shape == kStar && depth == 3) return (const void*)&rs3t_kernel<T, kStar, 3>; \
             if (r == 1 && shape == kBox && depth == 2) return (const void*)&rs3t_kernel<T, kBox, 2>;   \

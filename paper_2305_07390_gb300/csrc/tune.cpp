@@ -299,7 +299,7 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
     naive.variant = 1;
     cand.push_back(naive);
     ++n;
-    // The 3D register-streaming build (FP64 depth 1, FP32 depths 2-3): z segments sized so
+    // The 3D register-streaming build (FP64 depth 1, FP32/BF16 depths 2-3): z segments sized so
     // that one step has about 1, 2 or 4 tiles per resident warp.
     if (plan->ndim == 3 && rs3_built((int)plan->esize, plan->shape, plan->radius)) {
         const DeviceInfo& dv = device_info();

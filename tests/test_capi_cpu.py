@@ -106,9 +106,8 @@ def test_register_streaming_params():
     with pytest.raises(ebisu.EbisuError) as ei:
         big.set_params(variant=2, depth=lo, tile_s=lo)
     assert ei.value.code == ebisu.ERR_UNSUPPORTED
-    # no 3D build; periodic grids must be at least 64 x 136
-    # 3D FP32: the 7-point star at depths 2 and 3, the 27-point box at depth 2
-    # (64 - 2t column strips of 4-row patches); no BF16 3D build
+    # 3D FP32 and BF16: the 7-point star at depths 2 and 3, the 27-point box at
+    # depth 2 (64 - 2t column strips, 2 fewer at even t, of 4-row patches)
     p3 = ebisu.Plan(3, (20, 20, 80), 0, 1, [0.1] * 7, ebisu.F32, ebisu.DIRICHLET)
     assert p3.rs_depths() == (2, 3)
     p3.set_params(variant=2, depth=3, tile_s=5)
@@ -117,7 +116,12 @@ def test_register_streaming_params():
         p3.set_params(variant=2, depth=4)
     assert ebisu.Plan(3, (20, 20, 20), 1, 1, [0.03] * 27, ebisu.F32, ebisu.DIRICHLET).rs_depths() == (2, 2)
     assert ebisu.Plan(3, (20, 20, 20), 0, 2, [0.07] * 13, ebisu.F32, ebisu.DIRICHLET).rs_depths() == (0, 0)
-    assert ebisu.Plan(3, (20, 20, 20), 0, 1, [0.1] * 7, ebisu.BF16, ebisu.DIRICHLET).rs_depths() == (0, 0)
+    assert ebisu.Plan(3, (20, 20, 20), 0, 1, [0.1] * 7, ebisu.BF16, ebisu.DIRICHLET).rs_depths() == (2, 3)
+    pb = ebisu.Plan(3, (20, 20, 80), 1, 1, [0.03] * 27, ebisu.BF16, ebisu.DIRICHLET)
+    assert pb.rs_depths() == (2, 2)
+    pb.set_params(variant=2, depth=2, tile_s=5)
+    assert (pb.params().tile_x, pb.params().tile_y) == (58, 4)
+    assert ebisu.Plan(3, (20, 20, 20), 0, 2, [0.07] * 13, ebisu.BF16, ebisu.DIRICHLET).rs_depths() == (0, 0)
     # 3D: FP64 radius 1 only, depth 1, 62-column strips of 2-row patches
     p3d = ebisu.Plan(3, (64, 64, 200), 1, 1, [0.03] * 27, ebisu.F64, ebisu.DIRICHLET)
     assert p3d.rs_depths() == (1, 1)

@@ -195,10 +195,10 @@ def test_rs3_in_place_and_unsupported(steps):
     assert plan.sync(ws) == 0
     ref = oracle.run(g, 0, 1, c, 0, steps)
     assert oracle.rel_linf(y.cpu().numpy(), ref, 1) <= TOL[0]
-    # no 3D build for the 125-point box or FP32
+    # no 3D build for the 125-point box, nor for the BF16 13-point star
     p2 = eb.Plan(3, dims, 1, 2, [0.01] * 125, eb.F64, 0)
     assert p2.rs_depths() == (0, 0)
-    assert eb.Plan(3, dims, 1, 1, [0.03] * 27, eb.BF16, 0).rs_depths() == (0, 0)
+    assert eb.Plan(3, dims, 0, 2, [0.07] * 13, eb.BF16, 0).rs_depths() == (0, 0)
     with pytest.raises(eb.EbisuError):
         p2.set_params(variant=2, depth=1)
 
@@ -219,22 +219,24 @@ def test_rs3_wait_timeout_reports_status(monkeypatch):
     assert plan.sync(ws) == 0
 
 
-# ---- 3D register streaming with temporal blocking (FP32 7-point star, depth 2, 3)
+# ---- 3D register streaming with temporal blocking (FP32 and BF16 storage:
+# the 7-point star at depth 2, 3; the 27-point box at depth 2)
 
+@pytest.mark.parametrize("dtype", [1, 2])
 @pytest.mark.parametrize("shape", [0, 1])
 @pytest.mark.parametrize("boundary", [0, 1])
 @pytest.mark.parametrize("which", [0, 1])
 @pytest.mark.parametrize("steps", [1, 5, 7])
-def test_rs3t_parity(shape, boundary, which, steps):
+def test_rs3t_parity(dtype, shape, boundary, which, steps):
     eb = _eb()
     # ragged z segments and strips; a periodic grid's last segment, band and
     # strip must still cover depth * radius cells
     dims = (29, 45, 150) if boundary == 0 else (30, 44, 150)
-    g, c = synth.problem(3, dims, shape, 1, boundary, seed=420 + boundary + 3 * which + 7 * shape)
-    x = torch.from_numpy(g).to(torch.float32).cuda()
+    g, c = synth.problem(3, dims, shape, 1, boundary, seed=420 + boundary + 3 * which + 7 * shape + 17 * dtype)
+    x = torch.from_numpy(g).to(eb.torch_dtype(dtype)).cuda()
     held = x.double().cpu().numpy()
     c_held = c.astype(np.float32).astype(np.float64)
-    plan = eb.Plan(3, dims, shape, 1, c, eb.F32, boundary)
+    plan = eb.Plan(3, dims, shape, 1, c, dtype, boundary)
     lo, hi = plan.rs_depths()
     assert (lo, hi) == ((2, 3) if shape == 0 else (2, 2))
     d = (lo, hi)[which]
@@ -242,10 +244,10 @@ def test_rs3t_parity(shape, boundary, which, steps):
     p = plan.params()
     assert (p.variant, p.tile_x, p.tile_y, p.depth) == (2, 64 - 2 * d - (2 if d % 2 == 0 else 0), 4, d)
     y = run(plan, x, steps)
-    assert torch.equal(y, run(plan, x, steps, naive=True)), "3D FP32 register-streaming and naive kernels differ"
+    assert torch.equal(y, run(plan, x, steps, naive=True)), "3D register-streaming and naive kernels differ"
     ref = oracle.run(held, shape, 1, c_held, boundary, steps)
     pad = 1 if boundary == 0 else 0
-    assert oracle.rel_linf(y.double().cpu().numpy(), ref, pad) <= TOL[1]
+    assert oracle.rel_linf(y.double().cpu().numpy(), ref, pad) <= TOL[dtype]
     if boundary == 0:
         m = np.ones(held.shape, bool)
         m[1:-1, 1:-1, 1:-1] = False
