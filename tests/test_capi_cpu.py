@@ -136,3 +136,23 @@ def test_register_streaming_params():
     # FP64 builds shallow depths only (its FMA pipe, not HBM, bounds it)
     p64 = ebisu.Plan(2, (500, 500), 1, 2, [0.04] * 25, ebisu.F64, ebisu.DIRICHLET)
     assert p64.rs_depths() == (1, 1)
+
+
+def test_bench_names_the_kernel_a_plan_launches():
+    """The benchmark labels each row with the kernel its plan's parameters
+    select (host logic only: no launch)."""
+    import bench
+    p2 = ebisu.Plan(2, (300, 300), 0, 1, [0.2] * 5, ebisu.F32, ebisu.DIRICHLET)
+    p2.set_params(variant=2, depth=p2.rs_depths()[1], tile_s=32)
+    assert bench.kernel_name(p2) == "rs_kernel"
+    p2.set_params(variant=1)
+    assert bench.kernel_name(p2) == "naive_kernel"
+    p64 = ebisu.Plan(3, (20, 20, 80), 0, 1, [0.1] * 7, ebisu.F64, ebisu.DIRICHLET)
+    p64.set_params(variant=2, depth=1, tile_s=8)
+    assert bench.kernel_name(p64) == "rs3_kernel"
+    for dt in (ebisu.F32, ebisu.BF16):
+        p3 = ebisu.Plan(3, (20, 20, 80), 0, 1, [0.1] * 7, dt, ebisu.DIRICHLET)
+        p3.set_params(variant=2, depth=3, tile_s=5)
+        assert bench.kernel_name(p3) == "rs3t_kernel"
+        p3.set_params(tile_x=16, tile_y=8, tile_s=8, depth=2)
+        assert bench.kernel_name(p3) == "tb_kernel"
