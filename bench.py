@@ -29,17 +29,30 @@ UNIT = "cell-updates/s"
 N = 8192
 SOLVE_STEPS = 1000
 STENCILS = [("star", 0, 1), ("star", 0, 2), ("star", 0, 3), ("box", 1, 1), ("box", 1, 2)]
-FP64_PEAK_FLOPS = 1.25e12  # nominal GB300 FP64 rate (vector = tensor on this part)
+FP64_PEAK_FALLBACK = 1.255e12  # DFMA probe on this GPU model at 2070 MHz (2 DFMA/clk/SM x 152 SMs)
 
 
 # DRAM bytes per cell update measured by ncu for a kernel build
-# (dram__bytes_read.sum + dram__bytes_write.sum of a capture, divided by the
-# capture's cell updates; the traffic grows in proportion with cells x steps
-# at the depth the bench runs).  Only for builds unchanged since the capture.
+# (dram__bytes_read.sum + dram__bytes_write.sum of a capture of a 4096^2
+# case, divided by that capture's cell updates; the traffic grows in
+# proportion with cells x steps at the depth the bench runs).  Only for
+# builds unchanged since the capture.
 TRAFFIC_BYTES_PER_UPDATE = {
-    # profiles/tb_kernel_fp64_2d_box_r2_4096.md: 1.081 GB / (4096^2 x 4)
+    # 1.081 GB over 4 steps of a 4096^2 interior
     "tb_kernel<double,2D,box r2>": 1.081e9 / (4096 * 4096 * 4),
 }
+
+
+def fp64_peak(probe, clk):
+    """FP64 FMA peak for the roofline: the in-run DFMA probe (the figure the
+    cost model also uses), scaled from the clock the probe saw to the median
+    SM clock sampled during the timed region."""
+    f = probe.get("f64_flops") or FP64_PEAK_FALLBACK
+    hz = probe.get("sm_hz") or 0.0
+    mhz = (clk or {}).get("sm_mhz")
+    scale = (mhz * 1e6 / hz) if (mhz and hz > 0) else 1.0
+    return f * scale, {"peak_source": "probe", "probe_f64_flops": f, "probe_sm_mhz": hz / 1e6,
+                       "timed_sm_mhz": mhz, "clock_scale": scale}
 
 
 def hbm_peak():
@@ -226,6 +239,7 @@ def run_set3d(args):
     n, steps = 512, 200
     stream = torch.cuda.current_stream()
     sh = ebisu.current_stream_handle()
+    peak, _ = fp64_peak(ebisu.ebisu_probe_device(), None)
     rows = []
     for name, shape, r, bd in (("star r1", 0, 1, 0), ("star r2", 0, 2, 0), ("box r1", 1, 1, 0),
                                ("box r2", 1, 2, 0), ("star r1 periodic", 0, 1, 1)):
@@ -258,7 +272,7 @@ def run_set3d(args):
         P = npoints3(shape, r)
         rate = n ** 3 * steps / (ms * 1e-3)
         rows.append({"stencil": name, "points": P, "ms": ms, "cell_updates_per_s": rate,
-                     "roofline_frac": rate * 2 * P / FP64_PEAK_FLOPS,
+                     "roofline_frac": rate * 2 * P / peak,
                      "naive_cell_updates_per_s": n ** 3 * ns / (ms_naive * 1e-3),
                      "tuner_preferred": VARIANT_NAMES[pref], "kernel": kernel_name(plan),
                      "params": plan.params().as_dict()})
@@ -531,6 +545,56 @@ def cpu_baseline(budget_s=15.0):
                       f"FP64 grid (of the {SOLVE_STEPS} per solve)"}
 
 
+def precision_form_list(ebisu):
+    """(name, storage type, rounding) of the reduced-precision forms the bench
+    runs beside the FP64 set: FP32 and BF16 storage rounded to nearest even,
+    and BF16 storage with stochastic rounding where the library has it."""
+    out = [("f32", ebisu.F32, None), ("bf16", ebisu.BF16, None)]
+    if hasattr(ebisu, "ROUND_STOCHASTIC"):
+        out.append(("bf16-sr", ebisu.BF16, "sr"))
+    return out
+
+
+class OracleCones:
+    """The oracle on a W x W corner window of a benchmarked solve: the
+    window's dependency cone (r cells per step, plus the pad) is cut out of
+    the stored input, rounded to the storage type, and stepped by the oracle
+    in FP64 with the FP32-rounded coefficients; inside the window the cut's
+    artificial edge is never reached, so the values are exact.  The cones run
+    on the host cores in a background thread (the oracle releases the GIL)
+    while the GPU work proceeds."""
+
+    W = 6
+
+    def __init__(self):
+        self.jobs, self.res, self.th, self.seconds = [], {}, None, 0.0
+
+    def add(self, key, g, c, shape, r, steps, tdtype):
+        import numpy as np
+        import torch
+        span = self.W + 2 * r + steps * r
+        cut = np.ascontiguousarray(g[:span, :span])
+        held = torch.from_numpy(cut).to(tdtype).double().numpy()
+        self.jobs.append((key, held, c.astype(np.float32).astype(np.float64), shape, r, steps))
+
+    def _run(self):
+        import oracle
+        t0 = time.perf_counter()
+        for key, held, c, shape, r, steps in self.jobs:
+            ref = oracle.run(held, shape, r, c, 0, steps, nthreads=os.cpu_count())
+            self.res[key] = ref[r:r + self.W, r:r + self.W]
+        self.seconds = time.perf_counter() - t0
+
+    def start(self):
+        self.th = threading.Thread(target=self._run, daemon=True)
+        self.th.start()
+
+    def join(self):
+        if self.th is not None:
+            self.th.join()
+        return self.res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,9 +653,18 @@ def main():
 
     stream = torch.cuda.current_stream()
     sh = ebisu.current_stream_handle()
+    # FMA rates, shared-load bandwidth and barrier cost of this GPU: they feed
+    # the cost model the tuner ranks with and the FP64 roofline reported below
+    probe = ebisu.ebisu_probe_device()
+    steps = args.solve_steps
+    forms_dt = precision_form_list(ebisu)
+    cones = OracleCones() if (rank == 0 and not args.no_cpu) else None
     probs = []
     for name, shape, r in STENCILS:
         g, c = synth.problem(2, (N, N), shape, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED + 17 * r + shape)
+        if cones is not None:
+            for dname, dt, _ in forms_dt:
+                cones.add((dname, f"{name} r{r}"), g, c, shape, r, steps, ebisu.torch_dtype(dt))
         plan = ebisu.Plan(2, (N, N), shape, r, c, ebisu.F64, ebisu.DIRICHLET)
         host_in = torch.from_numpy(g).pin_memory()
         x = host_in.cuda()
@@ -600,7 +673,8 @@ def main():
         host_out = torch.empty_like(host_in).pin_memory()
         probs.append(dict(name=f"{name} r{r}", shape=shape, r=r, plan=plan, x=x, y=y, ws=ws,
                           host_in=host_in, host_out=host_out, P=npoints(shape, r)))
-    steps = args.solve_steps
+    if cones is not None:
+        cones.start()
     cells = N * N
     # Section 6's fine-tuning: the cost model ranks parameter sets, a short
     # timed run of the best few on this grid picks one (outside the timed region)
@@ -652,14 +726,16 @@ def main():
     total_ms, total_upd, _ = aggregate_replicas(total_ms, upd_per_step * args.steps, dist)
     value = total_upd / (total_ms * 1e-3)
 
-    # per-stencil rates and the roofline of the dominant kernel (largest time)
+    # per-stencil rates and the roofline of the dominant kernel (largest time),
+    # against the in-run FP64 probe at the timed region's clock
+    peak, peak_info = fp64_peak(probe, clk)
     per = []
     for p, ms_list in zip(probs, per_launch):
         ms = sum(ms_list) / len(ms_list)
         rate = cells * steps / (ms * 1e-3)
         flops = 2.0 * p["P"] * cells * steps
         per.append(dict(stencil=p["name"], points=p["P"], ms_per_launch=ms, cell_updates_per_s=rate,
-                        tflops=flops / (ms * 1e-3) / 1e12, roofline_frac=flops / (ms * 1e-3) / FP64_PEAK_FLOPS,
+                        tflops=flops / (ms * 1e-3) / 1e12, roofline_frac=flops / (ms * 1e-3) / peak,
                         params=p["plan"].params().as_dict()))
     # the one-step-per-launch kernel on the same grid (100 steps, scaled)
     for p, d in zip(probs, per):
@@ -700,13 +776,18 @@ def main():
     e2e_val = upd_per_step * ws_n / (max(e2e_ms) * 1e-3)
 
     # the FP32- and BF16-storage forms of the same solves (FP32 arithmetic):
-    # rate, speedup over the FP64 path, and error against the FP64 result
-    # (itself checked against the oracle by the full-size parity tests)
+    # rate, speedup over the FP64 path, roofline at the depth run, and error
+    # against the oracle (corner windows, FP64 on the values the device holds)
+    # and against the FP64 GPU result (whole grid, original coefficients)
     forms = []
-    for dt, dname in ((ebisu.F32, "f32"), (ebisu.BF16, "bf16")):
+    hbm, hbm_src = hbm_peak()
+    for dname, dt, rounding in forms_dt:
         rows = []
+        es = 4 if dt == ebisu.F32 else 2
         for p, d in zip(probs, per):
             plan = ebisu.Plan(2, (N, N), p["shape"], p["r"], p["plan"].coeffs, dt, ebisu.DIRICHLET)
+            if rounding == "sr":
+                plan.set_rounding(ebisu.ROUND_STOCHASTIC, synth.DEFAULT_SEED)
             xl = p["x"].to(ebisu.torch_dtype(dt))
             yl = torch.empty_like(xl)
             wsl = plan.workspace()
@@ -727,34 +808,41 @@ def main():
             rr = p["r"]
             ref = p["y"][rr:-rr, rr:-rr]
             err = float((yl[rr:-rr, rr:-rr].double() - ref).abs().max() / ref.abs().max())
+            win = yl[rr:rr + OracleCones.W, rr:rr + OracleCones.W].double().cpu().numpy()
             a.record(stream)
             plan.run(xl, yl, min(steps, 100), wsl, stream=sh, naive=True)
             b.record(stream)
             b.synchronize()
             naive_rate = cells * min(steps, 100) / (a.elapsed_time(b) * 1e-3)
             rate = cells * steps / (ms * 1e-3)
+            prm = plan.params().as_dict()
             rows.append(dict(stencil=p["name"], cell_updates_per_s=rate,
                              speedup_vs_fp64=rate / d["cell_updates_per_s"],
                              naive_cell_updates_per_s=naive_rate, speedup_vs_naive=rate / naive_rate,
                              rel_linf_vs_fp64=err, tuner_preferred=VARIANT_NAMES[tuned],
-                             kernel=kernel_name(plan), params=plan.params().as_dict()))
+                             kernel=kernel_name(plan), params=prm,
+                             roofline=stencil_roofline(rate, p["P"], es, prm["depth"], probe["f32_flops"], hbm)))
+            rows[-1]["_win"] = win
             del xl, yl, wsl, plan
         torch.cuda.empty_cache()
-        forms.append(dict(dtype=dname, per_stencil=rows,
+        forms.append(dict(dtype=dname, rounding="stochastic" if rounding == "sr" else "nearest even",
+                          per_stencil=rows,
                           set_cell_updates_per_s=len(rows) * cells * steps /
-                          sum(cells * steps / r_["cell_updates_per_s"] for r_ in rows)))
-
-    probe = ebisu.ebisu_probe_device()
-    hbm, hbm_src = hbm_peak()
+                          sum(cells * steps / r_["cell_updates_per_s"] for r_ in rows),
+                          roofline_peaks={"hbm_bytes_per_s": hbm, "hbm_source": hbm_src,
+                                          "fp32_flops": probe["f32_flops"], "fp32_source": "live probe (FMA loop)"}))
+    cone_refs = cones.join() if cones is not None else {}
     for f in forms:
-        es = 4 if f["dtype"] == "f32" else 2
-        for r_, p in zip(f["per_stencil"], probs):
-            r_["roofline"] = stencil_roofline(r_["cell_updates_per_s"], p["P"], es, r_["params"]["depth"],
-                                              probe["f32_flops"], hbm)
-        f["roofline_peaks"] = {"hbm_bytes_per_s": hbm, "hbm_source": hbm_src,
-                               "fp32_flops": probe["f32_flops"], "fp32_source": "live probe (FMA loop)"}
+        for r_ in f["per_stencil"]:
+            win = r_.pop("_win")
+            ref = cone_refs.get((f["dtype"], r_["stencil"]))
+            r_["rel_linf_vs_oracle"] = (None if ref is None else
+                                        float(np.max(np.abs(win - ref)) / np.max(np.abs(ref))))
+        f["oracle_check"] = (f"corner window {OracleCones.W}x{OracleCones.W} of each {N}x{N} solve after "
+                             f"{steps} steps; oracle in FP64 on the stored (rounded) input and the "
+                             "FP32-rounded coefficients, over the window's dependency cone")
     cpu = None
-    if rank == 0 and ws_n >= 1 and not args.no_cpu and ws_n == 1:
+    if rank == 0 and not args.no_cpu and ws_n == 1:
         cpu = cpu_baseline()
 
     line = {
@@ -766,11 +854,9 @@ def main():
                    "stencils": [p["name"] for p in probs], "seed": synth.DEFAULT_SEED,
                    "l2": "inputs larger than L2 (537 MB per grid, 129 MB L2)",
                    "parallelism": f"replicas x{ws_n}"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_FLOPS / 1e12, "unit": "TFLOP/s",
-                     "frac": achieved * 1e12 / FP64_PEAK_FLOPS, "traffic": dom_traffic,
-                     "kernel": dom_name,
-                     "peak_source": "nominal FP64 rate of the profiling recipe's table; live probe "
-                                    f"{probe['f64_flops'] / 1e12:.3f} TFLOP/s"},
+        "roofline": dict({"bound": "alu", "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
+                          "frac": achieved * 1e12 / peak, "traffic": dom_traffic, "kernel": dom_name},
+                         **peak_info),
         "per_stencil": per,
         "precision_forms": forms,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -26,7 +26,8 @@
  *   - Storage types: EBISU_F64 (double), EBISU_F32 (float), EBISU_BF16
  *     (bfloat16, 2 bytes).  F64 computes in double.  F32 and BF16 compute in
  *     float with the coefficients rounded to float, and round every step's
- *     result to the storage type (round to nearest even), including the
+ *     result to the storage type (round to nearest even, or for BF16 on
+ *     request stochastically: ebisu_plan_set_rounding), including the
  *     intermediate steps inside a temporal block.
  *   - Memory: every pointer to grid data or workspace is a device pointer
  *     owned by the caller (unless a function says host pointer).  Plans own
@@ -67,6 +68,7 @@ enum ebisu_status {
 enum ebisu_shape { EBISU_STAR = 0, EBISU_BOX = 1 };
 enum ebisu_dtype { EBISU_F64 = 0, EBISU_F32 = 1, EBISU_BF16 = 2 };
 enum ebisu_boundary { EBISU_DIRICHLET = 0, EBISU_PERIODIC = 1 };
+enum ebisu_rounding { EBISU_ROUND_NEAREST = 0, EBISU_ROUND_STOCHASTIC = 1 };
 
 /* Execution parameters of a plan (the tuner's search space, Sections 5-6):
  *   tile_x, tile_y : output tile extents in x and (3D only) y; the tile is
@@ -151,6 +153,34 @@ int ebisu_plan_grid_elems(ebisu_plan_t plan, int64_t* elems);
 int ebisu_plan_get_params(ebisu_plan_t plan, ebisu_params* p);
 int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* p);
 
+/* Storage rounding of a BF16 plan (the paper's kernels are FP64 only; this
+ * serves the reduced-precision forms).
+ *   rounding : EBISU_ROUND_NEAREST (the default: every step's FP32 result
+ *              rounded to nearest even) or EBISU_ROUND_STOCHASTIC (BF16
+ *              storage only, else EBISU_ERR_UNSUPPORTED).
+ *   seed     : seeds the random bits of stochastic rounding.
+ * Round-to-nearest BF16 storage stagnates on long runs: an update smaller
+ * than half a BF16 ulp (2^-9 relative) is discarded at every step, so the
+ * error against the exact solution grows with the step count.  Stochastic
+ * rounding rounds x up to the next BF16 value with probability equal to the
+ * discarded fraction of an ulp, which keeps the rounding unbiased.  The
+ * random bits are a function of (seed, step, cell) only:
+ *   pcg(v)   = PCG hash (Jarzynski and Olano, JCGT 9(3), 2020): s = v *
+ *              747796405 + 2891336453; w = ((s >> ((s >> 28) + 4)) ^ s) *
+ *              277803737; pcg = (w >> 22) ^ w   (32-bit arithmetic)
+ *   K        = pcg(lo32(seed) ^ pcg(hi32(seed)))
+ *   K_t      = pcg(K ^ t), t = 1 .. steps, the step whose result is rounded
+ *   rnd      = pcg(i + K_t), i = the cell's index in the stored array mod 2^32
+ *   result   = BF16 with the upper 16 bits of (bits(x) + (rnd >> 16))
+ * so the blocked, naive and batched kernels round every cell of every step
+ * alike and return identical results.  Stochastic rounding runs in the
+ * register-streaming build (2D; 3D radius 1) and the one-step kernel; a plan
+ * on the shared-memory build moves to the register-streaming one (or to the
+ * one-step kernel where there is none), and ebisu_plan_set_params rejects
+ * variant 0 while the rounding is stochastic.  Host only. */
+int ebisu_plan_set_rounding(ebisu_plan_t plan, int rounding, uint64_t seed);
+int ebisu_plan_get_rounding(ebisu_plan_t plan, int* rounding, uint64_t* seed);
+
 /* Temporal depths built for the register-streaming kernel (variant 2) of
  * this plan's stencil and storage type (Section 4's temporal blocking with
  * the per-level queues held in registers): *shallow <= *deep.  3D plans: 1
@@ -201,16 +231,30 @@ int ebisu_run_naive(ebisu_plan_t plan, const void* in, void* out,
  * cells (a 2048 x 2048 FP64 grid fits).  Larger plans return
  * EBISU_ERR_UNSUPPORTED and nothing is enqueued.
  *   plan, in, out, steps, stream : as for ebisu_run (in == out allowed).
- *   wait : 0 = enqueue and return; nonzero = also wait for the stream and
- *          return the kernels' status (as ebisu_sync would).
- * The first call on a device looks up the array's device address (a host
- * call, done once per device with that device current).  Every call on a
- * device uses the same array, and the array keeps what the last call left
- * in it; each call resets the part that must start at zero (the control
- * block) itself.  Calls whose work overlaps on the GPU, on different streams
- * or threads, race on the array: serialise them. */
+ *   wait : 0 = enqueue and return (the kernels' status stays in the array
+ *          until ebisu_sync_static reads it or the next call on the device
+ *          resets it, so read it before the next call); nonzero = also
+ *          wait for the stream and return the kernels' status (as ebisu_sync
+ *          would).
+ * Every call looks up the array's device address with the caller's device
+ * current (a host-side query that allocates nothing).  The array is reserved
+ * when this part of the library is loaded on a device: at the first call
+ * there under lazy module loading (the default), or when the context is
+ * created under CUDA_MODULE_LOADING=EAGER.  The first call on a device
+ * should therefore come before any stream capture.  The serving loop's HBM
+ * budget does not count the array.  Every call on a device uses the same
+ * array, and the array keeps what the last call left in it; each call resets
+ * the part that must start at zero (the control block) itself.  Calls whose
+ * work overlaps on the GPU, on different streams or threads, race on the
+ * array: serialise them. */
 int ebisu_run_static(ebisu_plan_t plan, const void* in, void* out,
                      int64_t steps, void* stream, int wait);
+
+/* Status read for ebisu_run_static with wait = 0 (no counterpart in the
+ * paper): wait for `stream`, then read and clear the status word the last
+ * static run on the current device left in the library's array.  Returns
+ * what ebisu_sync returns.  Allocates nothing. */
+int ebisu_sync_static(void* stream);
 
 /* Wait for `stream`, then read and clear the status word that kernels of
  * the last run on `workspace` left there.  Returns EBISU_OK, EBISU_ERR_CUDA
@@ -366,6 +410,9 @@ int ebisu_serve_destroy(ebisu_server_t s);
  *   out[0] FP64 FMA rate (flop/s, 2 per FMA), out[1] FP32 FMA rate,
  *   out[2] shared-memory load bandwidth (byte/s), out[3] device-wide
  *   barrier latency (seconds), out[4] SM count, out[5] SM clock seen (Hz).
+ * The rates also replace the figures the cost model (ebisu_plan_model, the
+ * tuner's ranking) uses on this device for the rest of the process, so that
+ * a roofline computed from them and the model agree.
  * Synchronises the device. */
 int ebisu_probe_device(double* out);
 

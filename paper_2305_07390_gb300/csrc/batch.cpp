@@ -63,11 +63,11 @@ struct ebisu_batch_s {
 namespace {
 
 struct Key {
-    int ndim, shape, radius, dtype, rs, variant;
+    int ndim, shape, radius, dtype, rounding, rs, variant;
     bool operator<(const Key& o) const
     {
-        return std::tie(ndim, shape, radius, dtype, rs, variant) <
-               std::tie(o.ndim, o.shape, o.radius, o.dtype, o.rs, o.variant);
+        return std::tie(ndim, shape, radius, dtype, rounding, rs, variant) <
+               std::tie(o.ndim, o.shape, o.radius, o.dtype, o.rounding, o.rs, o.variant);
     }
 };
 
@@ -111,6 +111,8 @@ int layout(ebisu_batch_s* b)
         // (a plan whose tuner preferred the one-step kernel keeps the best
         // fused parameters too)
         const bool rs = uses_rs(&b->plans[i]);
+        // stochastic rounding exists in the register-streaming build only
+        if (!rs && plan_sr(&b->plans[i]) && b->steps[i] > 0) return EBISU_ERR_UNSUPPORTED;
         if (rs) {
             b->plans[i].prm.variant = 2;
         } else {
@@ -119,7 +121,7 @@ int layout(ebisu_batch_s* b)
         }
         const ebisu_plan_s* p = &b->plans[i];
         if (b->steps[i] <= 0) continue;  // zero steps: plain copy, no kernel
-        Key k{p->ndim, p->shape, p->radius, p->dtype, rs ? 1 : 0,
+        Key k{p->ndim, p->shape, p->radius, p->dtype, plan_sr(p) ? 1 : 0, rs ? 1 : 0,
               rs ? p->prm.depth : kernel_variant(p->dtype, p->prm.ctas_per_sm)};
         auto it = gid.find(k);
         if (it == gid.end()) {

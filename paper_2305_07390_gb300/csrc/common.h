@@ -130,6 +130,8 @@ struct RSGrid {
     int32_t nblocks;    // ceil(steps / depth)
     int32_t depth_last; // steps done by the last block (<= depth)
     int32_t tile_base;  // index of this problem's first tile counter
+    uint32_t sr_key;    // stochastic-rounding plan key (BF16-SR storage only)
+    int32_t reserved_;
     double coef[kMaxPoints];
     float coef_f[kMaxPoints];  // the same rounded to FP32 (FP32/BF16 storage)
 };
@@ -163,6 +165,8 @@ struct RS3Params {
     int32_t nblocks;     // ceil(steps / depth)
     int32_t depth_last;  // steps done by the last block (<= depth)
     int32_t debug_stall;
+    uint32_t sr_key;     // stochastic-rounding plan key (BF16-SR storage only)
+    int32_t reserved_;
     double coef[kMaxPoints];
     float coef_f[kMaxPoints];
 };

@@ -13,6 +13,8 @@ struct NaiveParams {
     int64_t lds, ld1;
     int32_t pad;
     int32_t periodic;
+    uint32_t sr_k;             // stochastic rounding: this step's key K_t (BF16-SR storage only)
+    int32_t reserved_;
     double coef[kMaxPoints];
     float coef_f[kMaxPoints];  // the same rounded to FP32 on the host (FP32/BF16 storage)
 };
@@ -45,6 +47,7 @@ struct PadParams {
 EBISU_DECLARE_RS_PTRS(f64)
 EBISU_DECLARE_RS_PTRS(f32)
 EBISU_DECLARE_RS_PTRS(bf16)
+EBISU_DECLARE_RS_PTRS(bf16sr)
 
 #define EBISU_DECLARE_RS_ENTRY(NAME)                                                               \
     cudaError_t rs_launch_##NAME(int s, int r, int d, const RSParams& p, int g, cudaStream_t st);   \
@@ -55,6 +58,11 @@ EBISU_DECLARE_RS_PTRS(bf16)
 EBISU_DECLARE_RS_ENTRY(f64)
 EBISU_DECLARE_RS_ENTRY(f32)
 EBISU_DECLARE_RS_ENTRY(bf16)
+EBISU_DECLARE_RS_ENTRY(bf16sr)
+
+// BF16 storage with stochastic rounding: the one-step kernel (kern_bf16sr.cu;
+// pad copies and reductions use the BF16 ones, the storage is the same)
+cudaError_t naive_launch_bf16sr(int d, int s, int r, const void* a, void* b, const NaiveParams& p, cudaStream_t st);
 
 EBISU_DECLARE_DTYPE_ENTRY(f64)
 EBISU_DECLARE_DTYPE_ENTRY(f32)

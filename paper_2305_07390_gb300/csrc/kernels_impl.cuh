@@ -60,7 +60,9 @@ __global__ void __launch_bounds__(256) naive_kernel(const T* __restrict__ src, T
             acc = D::mul(cf(0), at(0));
 #pragma unroll
             for (int k = 1; k < P; ++k) acc = D::fma(cf(k), at(k), acc);
-            dst[ps * lds + (int64_t)q1 * ld1 + q2] = D::narrow(acc);
+            const int64_t o = ps * lds + (int64_t)q1 * ld1 + q2;
+            if constexpr (D::kSR) acc = sr_round_bf16(acc, (uint32_t)o + a.sr_k);
+            dst[o] = D::narrow(acc);
         } else {
             const int64_t c = (ps + pad) * lds + (int64_t)(q1 + pad1) * ld1 + (q2 + pad);
             const T* p = src + c;
@@ -68,6 +70,7 @@ __global__ void __launch_bounds__(256) naive_kernel(const T* __restrict__ src, T
             acc = D::mul(cf(0), at(0));
 #pragma unroll
             for (int k = 1; k < P; ++k) acc = D::fma(cf(k), at(k), acc);
+            if constexpr (D::kSR) acc = sr_round_bf16(acc, (uint32_t)c + a.sr_k);
             dst[c] = D::narrow(acc);
         }
     }

@@ -11,8 +11,6 @@
 // device that loads this part of the library and held until the process
 // exits.  Nothing in this file allocates; the run itself is ebisu_run, given
 // the array's device address as its workspace.
-#include <mutex>
-
 #include "plan.h"
 
 namespace {
@@ -23,27 +21,21 @@ constexpr size_t kStaticScratchBytes = 64ull << 20;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_mu;
-void* g_addr[64] = {nullptr};  // device address of the array, per device
-
-// Look up the array's device address for the current device (once per
-// device).  In host code `g_static_scratch` names a host-side stand-in, not
-// device memory, so it must never be passed to a kernel directly.
+// The array's device address in the current device's current context.  In
+// host code `g_static_scratch` names a host-side stand-in, not device memory,
+// so it must never be passed to a kernel directly.  The lookup is a host-side
+// query that allocates nothing; it is repeated on every call (with the
+// caller's device current) rather than cached, so that a device that was
+// reset, or a context other than the primary one, always yields the address
+// of its own copy of the array.  The first lookup in a context loads this
+// part of the library there, which is what reserves the array.
 int scratch_address(void** out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return ebisu::fail_cuda(e);
-    if (dev < 0 || dev >= 64) return EBISU_ERR_UNSUPPORTED;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return ebisu::fail_cuda(e);
-        if (!p) return EBISU_ERR_CUDA;
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    if (!p) return EBISU_ERR_CUDA;
+    *out = p;
     return EBISU_OK;
 }
 
@@ -61,5 +53,13 @@ extern "C" int ebisu_run_static(ebisu_plan_t plan, const void* in, void* out, in
     if (rc != EBISU_OK) return rc;
     rc = ebisu_run(plan, in, out, steps, ws, stream);
     if (rc != EBISU_OK || !wait) return rc;
+    return ebisu_sync(ws, stream);
+}
+
+extern "C" int ebisu_sync_static(void* stream)
+{
+    void* ws = nullptr;
+    const int rc = scratch_address(&ws);
+    if (rc != EBISU_OK) return rc;
     return ebisu_sync(ws, stream);
 }

@@ -1,5 +1,6 @@
 // plan.cpp -- plans, runs and the core of the C ABI (include/ebisu.h).
 #include "plan.h"
+#include "stencil.cuh"  // the stochastic-rounding keys (host side)
 
 #include <algorithm>
 #include <cstdlib>
@@ -172,6 +173,8 @@ int check_params(const ebisu_plan_s* p, const ebisu_params& q)
 {
     if (q.variant < 0 || q.variant > 2) return EBISU_ERR_INVALID_ARG;
     if (q.variant == 1) return EBISU_OK;
+    // stochastic rounding is built into the register-streaming and one-step kernels only
+    if (plan_sr(p) && q.variant == 0) return EBISU_ERR_UNSUPPORTED;
     if (q.variant == 2) {
         if (q.ctas_per_sm < 1 || q.ctas_per_sm > 16 || q.tile_s < 0) return EBISU_ERR_INVALID_ARG;
         return rs_layout(p, q, nullptr);
@@ -267,9 +270,13 @@ static NaiveParams naive_params(const ebisu_plan_s* p)
     return a;
 }
 
-cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, cudaStream_t st)
+cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, int64_t t, cudaStream_t st)
 {
-    const NaiveParams a = naive_params(p);
+    NaiveParams a = naive_params(p);
+    if (plan_sr(p)) {
+        a.sr_k = sr_step_key(p->sr_key, (uint32_t)t);
+        return naive_launch_bf16sr(p->ndim, p->shape, p->radius, src, dst, a, st);
+    }
     switch (p->dtype) {
     case EBISU_F64: return naive_launch_f64(p->ndim, p->shape, p->radius, src, dst, a, st);
     case EBISU_F32: return naive_launch_f32(p->ndim, p->shape, p->radius, src, dst, a, st);
@@ -309,6 +316,7 @@ namespace ebisu {
 
 cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int grid, cudaStream_t st)
 {
+    if (plan_sr(p)) return rs_launch_bf16sr(p->shape, p->radius, depth, prm, grid, st);
     switch (p->dtype) {
     case EBISU_F64: return rs_launch_f64(p->shape, p->radius, depth, prm, grid, st);
     case EBISU_F32: return rs_launch_f32(p->shape, p->radius, depth, prm, grid, st);
@@ -318,6 +326,7 @@ cudaError_t rs_launch(const ebisu_plan_s* p, int depth, const RSParams& prm, int
 
 cudaError_t rs3_launch(const ebisu_plan_s* p, int depth, const RS3Params& prm, int grid, cudaStream_t st)
 {
+    if (plan_sr(p)) return rs3_launch_bf16sr(p->shape, p->radius, depth, prm, grid, st);
     switch (p->dtype) {
     case EBISU_F64: return rs3_launch_f64(p->shape, p->radius, depth, prm, grid, st);
     case EBISU_F32: return rs3_launch_f32(p->shape, p->radius, depth, prm, grid, st);
@@ -328,6 +337,7 @@ cudaError_t rs3_launch(const ebisu_plan_s* p, int depth, const RS3Params& prm, i
 
 cudaError_t rs3_occupancy(const ebisu_plan_s* p, int depth, int* blocks)
 {
+    if (plan_sr(p)) return rs3_occupancy_bf16sr(p->shape, p->radius, depth, blocks);
     switch (p->dtype) {
     case EBISU_F64: return rs3_occupancy_f64(p->shape, p->radius, depth, blocks);
     case EBISU_F32: return rs3_occupancy_f32(p->shape, p->radius, depth, blocks);
@@ -338,6 +348,7 @@ cudaError_t rs3_occupancy(const ebisu_plan_s* p, int depth, int* blocks)
 
 cudaError_t rs_occupancy(const ebisu_plan_s* p, int depth, bool batch, int* blocks)
 {
+    if (plan_sr(p)) return rs_occupancy_bf16sr(p->shape, p->radius, depth, batch, blocks);
     switch (p->dtype) {
     case EBISU_F64: return rs_occupancy_f64(p->shape, p->radius, depth, batch, blocks);
     case EBISU_F32: return rs_occupancy_f32(p->shape, p->radius, depth, batch, blocks);
@@ -365,6 +376,7 @@ int64_t fill_rs_grid(const ebisu_plan_s* p, const RSLayout& L, const void* in, v
     g->nsegs = L.nsegs;
     g->nblocks = (int32_t)nb;
     g->depth_last = (int32_t)(steps - (nb - 1) * D);
+    g->sr_key = p->sr_key;
     for (int k = 0; k < p->npts; ++k) {
         g->coef[k] = p->coef[k];
         g->coef_f[k] = (float)p->coef[k];
@@ -436,6 +448,7 @@ static int run_rs3(ebisu_plan_t p, const void* in, void* out, int64_t steps, voi
     prm.nblocks = (int32_t)nb;
     prm.depth_last = (int32_t)(steps - (nb - 1) * D);
     prm.debug_stall = debug_stall;
+    prm.sr_key = p->sr_key;
     for (int k = 0; k < p->npts; ++k) {
         prm.coef[k] = p->coef[k];
         prm.coef_f[k] = (float)p->coef[k];
@@ -656,6 +669,54 @@ int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* q)
     return EBISU_OK;
 }
 
+int ebisu_plan_set_rounding(ebisu_plan_t plan, int rounding, uint64_t seed)
+{
+    if (!plan) return EBISU_ERR_INVALID_ARG;
+    if (rounding != EBISU_ROUND_NEAREST && rounding != EBISU_ROUND_STOCHASTIC) return EBISU_ERR_INVALID_ARG;
+    if (rounding == EBISU_ROUND_STOCHASTIC && plan->dtype != EBISU_BF16) return EBISU_ERR_UNSUPPORTED;
+    plan->rounding = rounding;
+    plan->sr_seed = seed;
+    plan->sr_key = sr_plan_key(seed);
+    if (!plan_sr(plan)) return EBISU_OK;
+    // the shared-memory build has no stochastic-rounding form: move the plan
+    // to the register-streaming build where one exists, else to the
+    // one-step kernel
+    const ebisu_params& q = plan->prm;
+    if (q.variant == 2 || (q.variant == 1 && q.fused_variant == 2)) return EBISU_OK;
+    ebisu_params v{};
+    v.variant = 2;
+    v.fused_variant = 2;
+    v.ctas_per_sm = 8;
+    v.threads = kRSThreads;
+    const int es = (int)plan->esize;
+    if (plan->ndim == 2) {
+        v.depth = rs_preferred_depth(es, plan->shape, plan->radius);
+        v.tile_s = (int32_t)std::max<int64_t>((int64_t)v.depth * plan->radius, std::min<int64_t>(plan->n[0], 64));
+    } else {
+        v.depth = rs3_built(es, plan->shape, plan->radius) ? rs3_depth(es, plan->shape, 1) : 1;
+        v.tile_s = (int32_t)std::min<int64_t>(plan->n[0], 64);
+    }
+    RSLayout L;
+    if (rs_layout(plan, v, &L) == EBISU_OK) {
+        v.tile_x = L.S;
+        v.tile_y = L.TY;
+        v.tile_s = L.H;
+        plan->prm = v;
+    } else {
+        plan->prm.variant = 1;  // no fused build of this stencil: the one-step kernel
+        plan->prm.fused_variant = 0;
+    }
+    return EBISU_OK;
+}
+
+int ebisu_plan_get_rounding(ebisu_plan_t plan, int* rounding, uint64_t* seed)
+{
+    if (!plan || !rounding) return EBISU_ERR_INVALID_ARG;
+    *rounding = plan->rounding;
+    if (seed) *seed = plan->sr_seed;
+    return EBISU_OK;
+}
+
 int ebisu_plan_rs_depths(ebisu_plan_t plan, int* shallow, int* deep)
 {
     if (!plan || !shallow || !deep) return EBISU_ERR_INVALID_ARG;
@@ -713,7 +774,7 @@ static int run_common(ebisu_plan_t p, const void* in, void* out, int64_t steps, 
         if (e != cudaSuccess) return fail_cuda(e);
         for (int64_t s = 0; s < steps; ++s) {
             void* dst = ((steps - 1 - s) % 2 == 0) ? out : wsgrid;
-            e = naive_launch(p, src, dst, st);
+            e = naive_launch(p, src, dst, s + 1, st);
             if (e != cudaSuccess) return fail_cuda(e);
             src = dst;
         }
@@ -817,6 +878,7 @@ int ebisu_probe_device(double* out)
     if (!out) return EBISU_ERR_INVALID_ARG;
     cudaError_t e = probe_device(out);
     if (e != cudaSuccess) return fail_cuda(e);
+    record_device_rates(out);  // the cost model uses the same figures from now on
     return EBISU_OK;
 }
 

@@ -23,6 +23,11 @@ struct ebisu_plan_s {
     int pad = 0, pad1 = 0;
     size_t esize = 8;
     int64_t elems = 0;
+    // storage rounding (EBISU_ROUND_*): stochastic for BF16 storage only;
+    // sr_key = sr_plan_key(sr_seed), the kernels' plan key
+    int rounding = 0;
+    uint64_t sr_seed = 0;
+    uint32_t sr_key = 0;
 };
 
 namespace ebisu {
@@ -53,6 +58,9 @@ const DeviceInfo& device_info();
 // Measured throughputs for the cost model; runs the microbenchmarks once per
 // process (or uses defaults from a host without a GPU).
 const DeviceInfo& device_rates();
+// Replace the current device's rates with a probe's results (ebisu_probe_device
+// output layout), so the cost model and the caller's roofline use one figure.
+void record_device_rates(const double* probe_out);
 
 void set_cuda_error(cudaError_t e);
 int fail_cuda(cudaError_t e);
@@ -76,7 +84,11 @@ int64_t fill_grid_desc(const ebisu_plan_s* p, const void* in, void* out, void* w
 cudaError_t tb_launch(const ebisu_plan_s* p, int variant, const TBParams& prm, int grid, size_t smem,
                       cudaStream_t st);
 cudaError_t tb_occupancy(const ebisu_plan_s* p, int variant, size_t smem, int* blocks);
-cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, cudaStream_t st);
+// one step (t = 1 .. steps: the step whose result is written; stochastic
+// rounding keys its random bits on it)
+cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, int64_t t, cudaStream_t st);
+// does the plan store BF16 with stochastic rounding (its own kernel builds)?
+inline bool plan_sr(const ebisu_plan_s* p) { return p->dtype == EBISU_BF16 && p->rounding == EBISU_ROUND_STOCHASTIC; }
 cudaError_t pad_copy(const ebisu_plan_s* p, const void* src, void* d0, void* d1, cudaStream_t st);
 
 int64_t wait_timeout_ns();

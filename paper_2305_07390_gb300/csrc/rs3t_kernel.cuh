@@ -201,6 +201,12 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
         // a lane's two columns as one copy (8 bytes FP32, 4 bytes BF16) when
         // both exist and every row starts them on a pair boundary (aligned
         // buffer, even row pitch -- hence even plane pitch -- and even column)
+        // stochastic rounding (BF16-SR storage): the step keys of this block's levels
+        uint32_t srk[Dt::kSR ? D : 1];
+        if constexpr (Dt::kSR) {
+#pragma unroll
+            for (int s = 1; s <= D; ++s) srk[s - 1] = sr_step_key(prm.sr_key, (uint32_t)(blk * D + s));
+        }
         constexpr int PB = 2 * (int)sizeof(T);  // bytes of a lane's column pair
         const bool pairs = !per && colok == 3u && ((ld1 & 1) == 0) && ((coloff[0] & 1) == 0) &&
                            ((reinterpret_cast<uintptr_t>(src) & (PB - 1)) == 0);
@@ -326,10 +332,19 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
                                 acc[v] = (k == 0) ? Dt::mul(ck, val) : Dt::fma(ck, val, acc[v]);
                             }
                         }
+                        // the cell's index in the stored array (stochastic rounding)
+                        uint32_t sr_row = 0;
+                        if constexpr (Dt::kSR) {
+                            const int zw = per ? ((zs < 0) ? zs + n0 : (zs >= n0 ? zs - n0 : zs)) : zs + pad;
+                            sr_row = (uint32_t)((int64_t)zw * lds) + (uint32_t)rowoff[i + s] + srk[s - 1];
+                        }
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
                             const bool keep = copy || prow || ((padc >> v) & 1u);
-                            const C o = keep ? Q(s - 1, cs, ib, v) : Dt::widen(Dt::narrow(acc[v]));
+                            C rd;
+                            if constexpr (Dt::kSR) rd = sr_round_bf16(acc[v], sr_row + (uint32_t)coloff[v]);
+                            else rd = Dt::widen(Dt::narrow(acc[v]));
+                            const C o = keep ? Q(s - 1, cs, ib, v) : rd;
                             if (s < D) {
                                 Q(s < D ? s : 0, cs, i, v) = o;
                             } else if (zs >= za && zs < zb && i < TY && ya + i < n1 && ((outc >> v) & 1u)) {

@@ -64,10 +64,11 @@ struct RSGeom {
     // addresses, loop state and the item's geometry (the 25-point box keeps
     // more of its rows' values live across its 100 FMAs: found by compiling)
     static constexpr int P = Stencil<2, SHAPE, R>::P;
+    static constexpr bool SR = DT<T>::kSR;  // stochastic rounding: step keys and a column key
     static constexpr int regs(int D, bool batch)
     {
         return (D * U * RW + (ASYNC ? 0 : PF * RW) + (EXT ? 0 : 4 + 2 * R) + 4 + (batch ? P : 0)) * WORDS + 56 +
-               ((EXT && R == 2) ? 48 : 0) + (batch ? 16 : 0);
+               ((EXT && R == 2) ? 48 : 0) + (batch ? 16 : 0) + (SR ? D + 4 : 0);
     }
     static constexpr int minb(int D, bool batch)
     {
@@ -362,6 +363,27 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
         auto acc_ref = [&](int s, int cs, int m) -> C& {
             return (s < D) ? ring[s < D ? s : 0][cs][X0 + m] : accD[m];
         };
+        // A level's result rounded to the storage type: to nearest even, or
+        // (BF16-SR storage) stochastically with the bits of the cell's
+        // stored index and step -- the key of level s's step, the column part
+        // of this lane's first cell (periodic: wrapped) and the row's part.
+        uint32_t srk[Dt::kSR ? D : 1];
+        uint32_t sr_col = 0;
+        if constexpr (Dt::kSR) {
+#pragma unroll
+            for (int s = 1; s <= D; ++s) srk[s - 1] = sr_step_key(gd->sr_key, (uint32_t)(blk * D + s));
+            sr_col = (uint32_t)(per ? (cb < 0 ? cb + n2 : (cb >= n2 ? cb - n2 : cb)) : cb + pad);
+        }
+        auto round_cell = [&](int s, int y, int m, C a) -> C {
+            if constexpr (Dt::kSR) {
+                const int yw = per ? (y < 0 ? y + n0i : (y >= n0i ? y - n0i : y)) : y + pad;
+                uint32_t c = sr_col + (uint32_t)m;
+                if (per && c >= (uint32_t)n2) c -= (uint32_t)n2;
+                return sr_round_bf16(a, (uint32_t)yw * (uint32_t)lds + c + srk[s - 1]);
+            } else {
+                return Dt::widen(Dt::narrow(a));
+            }
+        };
         auto level_row = [&](int s, int cs, const bool head) {
             C e[EXT ? 1 : 4 + 2 * R];
             if (!EXT && head) {
@@ -504,10 +526,10 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
 #pragma unroll
                                 for (int m = 0; m < 4; ++m)
                                     o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m]
-                                                              : Dt::widen(Dt::narrow(acc_ref(s, cs, m)));
+                                                              : round_cell(s, y, m, acc_ref(s, cs, m));
                             } else {
 #pragma unroll
-                                for (int m = 0; m < 4; ++m) o[m] = Dt::widen(Dt::narrow(acc_ref(s, cs, m)));
+                                for (int m = 0; m < 4; ++m) o[m] = round_cell(s, y, m, acc_ref(s, cs, m));
                             }
                             put_row(s, cs, y, o);
                         }
@@ -553,7 +575,7 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                         level_row(s, cs, false);
 #pragma unroll
                         for (int m = 0; m < 4; ++m)
-                            o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m] : Dt::widen(Dt::narrow(acc_ref(s, cs, m)));
+                            o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m] : round_cell(s, y, m, acc_ref(s, cs, m));
                         put_row(s, cs, y, o);
                     }
                 }

@@ -94,6 +94,7 @@ struct DT;
 template <>
 struct DT<double> {
     using C = double;
+    static constexpr bool kSR = false;
     __device__ static __forceinline__ C load(const double* p) { return __ldcg(p); }
     __device__ static __forceinline__ double raw(const double* p) { return __ldcg(p); }
     __device__ static __forceinline__ C load_ro(const double* p) { return __ldg(p); }
@@ -107,6 +108,7 @@ struct DT<double> {
 template <>
 struct DT<float> {
     using C = float;
+    static constexpr bool kSR = false;
     __device__ static __forceinline__ C load(const float* p) { return __ldcg(p); }
     __device__ static __forceinline__ float raw(const float* p) { return __ldcg(p); }
     __device__ static __forceinline__ C load_ro(const float* p) { return __ldg(p); }
@@ -120,6 +122,7 @@ struct DT<float> {
 template <>
 struct DT<__nv_bfloat16> {
     using C = float;
+    static constexpr bool kSR = false;
     __device__ static __forceinline__ C load(const __nv_bfloat16* p)
     {
         unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p));
@@ -137,6 +140,95 @@ struct DT<__nv_bfloat16> {
     }
     __device__ static __forceinline__ C widen(__nv_bfloat16 v) { return __bfloat162float(v); }
     __device__ static __forceinline__ __nv_bfloat16 narrow(C v) { return __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ C mul(C a, C b) { return __fmul_rn(a, b); }
+    __device__ static __forceinline__ C fma(C a, C b, C c) { return __fmaf_rn(a, b, c); }
+    __host__ __device__ static __forceinline__ C coef(double v) { return (float)v; }
+};
+
+// ---------------------------------------------------------------------------
+// Stochastic rounding of FP32 results to BF16 storage (a plan option; the
+// paper's kernels are FP64 only).  Round-to-nearest storage discards every
+// update smaller than half a BF16 ulp, so long runs stagnate; rounding up
+// with probability equal to the discarded fraction of an ulp keeps the
+// rounding unbiased.  The random bits are a pure function of (seed, step,
+// stored cell index), so every kernel -- blocked, naive, batched -- rounds a
+// given cell of a given step the same way, and their results stay identical.
+//
+//   pcg_hash(v)   : the PCG hash of Jarzynski and Olano ("Hash Functions for
+//                   GPU Rendering", JCGT 9(3), 2020): one step of the 32-bit
+//                   LCG of the PCG family followed by its RXS-M-XS output
+//                   permutation (O'Neill, 2014).  A bijection of 32-bit words.
+//   plan key      : K = pcg_hash(lo32(seed) ^ pcg_hash(hi32(seed)))
+//   step key      : K_t = pcg_hash(K ^ t), t = 1 .. steps (the step whose
+//                   result is being rounded)
+//   cell bits     : rnd = pcg_hash(i + K_t), i = the cell's index in the
+//                   stored (padded) array, modulo 2^32
+//   rounding      : BF16 bits of (bits(x) + (rnd >> 16)) truncated to their
+//                   upper 16 bits (x finite).
+// The last xor-shift of pcg_hash only changes bits 0-9, so rnd >> 16 equals
+// the multiply's upper half; sr_bits16 computes just that.
+
+struct bf16sr {  // storage tag: BF16 values, stochastic rounding
+    unsigned short bits;
+};
+
+__host__ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v)
+{
+    const uint32_t s = v * 747796405u + 2891336453u;
+    const uint32_t w = ((s >> ((s >> 28) + 4u)) ^ s) * 277803737u;
+    return (w >> 22) ^ w;
+}
+
+__host__ __device__ __forceinline__ uint32_t sr_plan_key(uint64_t seed)
+{
+    return pcg_hash((uint32_t)seed ^ pcg_hash((uint32_t)(seed >> 32)));
+}
+
+__host__ __device__ __forceinline__ uint32_t sr_step_key(uint32_t plan_key, uint32_t t)
+{
+    return pcg_hash(plan_key ^ t);
+}
+
+// upper 16 bits of pcg_hash(v)
+__device__ __forceinline__ uint32_t sr_bits16(uint32_t v)
+{
+    const uint32_t s = v * 747796405u + 2891336453u;
+    const uint32_t w = ((s >> ((s >> 28) + 4u)) ^ s) * 277803737u;
+    return w >> 16;
+}
+
+// x rounded stochastically to BF16, returned as FP32; `cell_plus_key` is
+// i + K_t (modulo 2^32)
+__device__ __forceinline__ float sr_round_bf16(float x, uint32_t cell_plus_key)
+{
+    return __uint_as_float((__float_as_uint(x) + sr_bits16(cell_plus_key)) & 0xFFFF0000u);
+}
+
+template <>
+struct DT<bf16sr> {
+    using C = float;
+    static constexpr bool kSR = true;
+    __device__ static __forceinline__ C load(const bf16sr* p)
+    {
+        unsigned short b = __ldcg(reinterpret_cast<const unsigned short*>(p));
+        return __uint_as_float(((unsigned)b) << 16);
+    }
+    __device__ static __forceinline__ bf16sr raw(const bf16sr* p)
+    {
+        return bf16sr{__ldcg(reinterpret_cast<const unsigned short*>(p))};
+    }
+    __device__ static __forceinline__ C load_ro(const bf16sr* p)
+    {
+        unsigned short b = __ldg(reinterpret_cast<const unsigned short*>(p));
+        return __uint_as_float(((unsigned)b) << 16);
+    }
+    __device__ static __forceinline__ C widen(bf16sr v) { return __uint_as_float(((unsigned)v.bits) << 16); }
+    // exact for the values these kernels store (already BF16 after rounding
+    // or copied from BF16 storage)
+    __device__ static __forceinline__ bf16sr narrow(C v)
+    {
+        return bf16sr{(unsigned short)(__float_as_uint(v) >> 16)};
+    }
     __device__ static __forceinline__ C mul(C a, C b) { return __fmul_rn(a, b); }
     __device__ static __forceinline__ C fma(C a, C b, C c) { return __fmaf_rn(a, b, c); }
     __host__ __device__ static __forceinline__ C coef(double v) { return (float)v; }

@@ -38,10 +38,12 @@ const DeviceInfo& device_rates()
     DeviceInfo& r = g_rates[dev];
     if (!g_rates_done[dev]) {
         r = base;
-        // GB300 values measured with ebisu_probe_device (FMA rates at the
-        // boost clock, 16-byte shared loads, one wait round trip) serve until
-        // a measurement replaces them.
-        r.f64 = 1.19e12;
+        // GB300 figures measured with ebisu_probe_device (FMA rates at the
+        // 2070 MHz boost clock, 16-byte shared loads, one wait round trip)
+        // serve until a probe in this process replaces them
+        // (ebisu_probe_device records its results here; EBISU_PROBE=1 runs
+        // it on first use).
+        r.f64 = 1.255e12;
         r.f32 = 74.7e12;
         r.lds = 38.0e12;
         r.barrier_s = 2.5e-6;
@@ -60,6 +62,18 @@ const DeviceInfo& device_rates()
         g_rates_done[dev] = true;
     }
     return r;
+}
+
+void record_device_rates(const double* out)
+{
+    const DeviceInfo& base = device_info();
+    device_rates();  // initialise the entry first
+    std::lock_guard<std::mutex> lk(g_rate_mu);
+    DeviceInfo& r = g_rates[base.device < 0 ? 0 : base.device];
+    if (out[0] > 0) r.f64 = out[0];
+    if (out[1] > 0) r.f32 = out[1];
+    if (out[2] > 0) r.lds = out[2];
+    if (out[3] > 0) r.barrier_s = out[3];
 }
 
 static double hbm_bytes_per_s()
@@ -293,10 +307,19 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
     std::vector<double> pred(max_candidates);
     int n = rank_candidates(plan, steps, cand.data(), pred.data(), max_candidates);
     if (n < 1) return EBISU_ERR_UNSUPPORTED;
-    // The one-step-per-launch kernel is timed too: where the fused kernel
-    // cannot beat it (measured: 3D low-order FP64 stars), the plan runs it.
     ebisu_params naive = cand[0];
     naive.variant = 1;
+    const bool sr = plan_sr(plan);
+    if (sr) {
+        // stochastic rounding: no shared-memory build; the one-step kernel
+        // keeps the plan's current fused parameters
+        n = 0;
+        cand.clear();
+        naive = plan->prm;
+        naive.variant = 1;
+    }
+    // The one-step-per-launch kernel is timed too: where the fused kernel
+    // cannot beat it (measured: 3D low-order FP64 stars), the plan runs it.
     cand.push_back(naive);
     ++n;
     // The 3D register-streaming build (FP64 depth 1, FP32/BF16 depths 2-3): z segments sized so
@@ -411,7 +434,17 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc == EBISU_OK) {
+    if (rc == EBISU_OK && sr) {
+        // no shared-memory build to keep; the fused build, if any, is the
+        // register-streaming one
+        if (best_fused_ms < 1e300) {
+            plan->prm = best_fused;
+            plan->prm.fused_variant = 2;
+            if (bestp.variant == 1) plan->prm.variant = 1;
+        } else {
+            plan->prm = naive;
+        }
+    } else if (rc == EBISU_OK) {
         // keep the best shared-memory-kernel parameters (batches and the
         // server use them) and the best temporally blocked build's
         // parameters; `variant` says which kernel won (1: the one-step

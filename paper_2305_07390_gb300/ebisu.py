@@ -23,6 +23,7 @@ LIB_PATH = os.path.join(HERE, "libebisu.so")
 STAR, BOX = 0, 1
 F64, F32, BF16 = 0, 1, 2
 DIRICHLET, PERIODIC = 0, 1
+ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1
 
 
 class EbisuError(RuntimeError):
@@ -77,10 +78,13 @@ SIGNATURES = {
     "ebisu_plan_get_params": (_I, [_P, ctypes.POINTER(Params)]),
     "ebisu_plan_set_params": (_I, [_P, ctypes.POINTER(Params)]),
     "ebisu_plan_rs_depths": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "ebisu_plan_set_rounding": (_I, [_P, _I, ctypes.c_uint64]),
+    "ebisu_plan_get_rounding": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_uint64)]),
     "ebisu_plan_workspace_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "ebisu_run": (_I, [_P, _P, _P, _I64, _P, _P]),
     "ebisu_run_naive": (_I, [_P, _P, _P, _I64, _P, _P]),
     "ebisu_run_static": (_I, [_P, _P, _P, _I64, _P, _I]),
+    "ebisu_sync_static": (_I, [_P]),
     "ebisu_sync": (_I, [_P, _P]),
     "ebisu_plan_tune": (_I, [_P, _P, _P, _I64, _P, _I, ctypes.POINTER(_D), _P]),
     "ebisu_plan_model": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
@@ -261,6 +265,16 @@ class Plan:
         for k, v in kw.items():
             setattr(p, k, int(v))
         _check(lib().ebisu_plan_set_params(self.h, ctypes.byref(p)), "ebisu_plan_set_params")
+
+    def set_rounding(self, rounding, seed=0):
+        """Storage rounding: ROUND_NEAREST or (BF16 only) ROUND_STOCHASTIC."""
+        _check(lib().ebisu_plan_set_rounding(self.h, int(rounding), ctypes.c_uint64(int(seed))),
+               "ebisu_plan_set_rounding")
+
+    def rounding(self):
+        r, sd = _I(), ctypes.c_uint64()
+        _check(lib().ebisu_plan_get_rounding(self.h, ctypes.byref(r), ctypes.byref(sd)), "ebisu_plan_get_rounding")
+        return r.value, sd.value
 
     def rs_depths(self):
         """Temporal depths built for the register-streaming kernel (variant 2)."""

@@ -156,3 +156,38 @@ def test_bench_names_the_kernel_a_plan_launches():
         assert bench.kernel_name(p3) == "rs3t_kernel"
         p3.set_params(tile_x=16, tile_y=8, tile_s=8, depth=2)
         assert bench.kernel_name(p3) == "tb_kernel"
+
+
+def test_stochastic_rounding_host_rules():
+    c2 = [0.2] * 5
+    for dt in (ebisu.F64, ebisu.F32):
+        p = ebisu.Plan(2, (64, 300), 0, 1, c2, dt, 0)
+        with pytest.raises(ebisu.EbisuError) as ei:
+            p.set_rounding(ebisu.ROUND_STOCHASTIC, 1)
+        assert ei.value.code == ebisu.ERR_UNSUPPORTED
+        p.set_rounding(ebisu.ROUND_NEAREST)  # always allowed
+    p = ebisu.Plan(2, (64, 300), 0, 1, c2, ebisu.BF16, 0)
+    with pytest.raises(ebisu.EbisuError) as ei:
+        p.set_rounding(7, 1)
+    assert ei.value.code == ebisu.ERR_INVALID_ARG
+    p.set_rounding(ebisu.ROUND_STOCHASTIC, 99)
+    assert p.rounding() == (ebisu.ROUND_STOCHASTIC, 99)
+    assert p.params().variant == 2
+    # no shared-memory build with stochastic rounding
+    with pytest.raises(ebisu.EbisuError) as ei:
+        p.set_params(tile_x=64, tile_s=32, depth=2)
+    assert ei.value.code == ebisu.ERR_UNSUPPORTED
+    p.set_params(variant=1)  # the one-step kernel has it
+    # 3D: the register-streaming build for radius 1, else the one-step kernel
+    c3 = [1.0 / 7] * 7
+    p3 = ebisu.Plan(3, (32, 32, 96), 0, 1, c3, ebisu.BF16, 0)
+    p3.set_rounding(ebisu.ROUND_STOCHASTIC, 5)
+    assert p3.params().variant == 2
+    c125 = [1.0 / 125] * 125
+    p5 = ebisu.Plan(3, (32, 32, 96), 1, 2, c125, ebisu.BF16, 0)
+    p5.set_rounding(ebisu.ROUND_STOCHASTIC, 5)
+    assert p5.params().variant == 1
+    # back to nearest: every build is allowed again
+    p.set_rounding(ebisu.ROUND_NEAREST)
+    p.set_params(tile_x=64, tile_s=32, depth=2)
+    assert p.params().variant == 0

@@ -112,3 +112,61 @@ def test_3d_fullsize_periodic_fourier(shape, r, k):
         ref = lamT.real * torch.cos(ph) - lamT.imag * torch.sin(ph)
         err = max(err, float(torch.max(torch.abs(y[z0:z0 + 64] - ref))))
     assert err / abs(lamT) <= TOL  # relative L-inf against the mode's amplitude
+
+
+def bench_tuned_plan(eb, ndim, dims, shape, r, c, x, dtype, tune_steps, candidates):
+    """A plan tuned the way bench.py tunes it (cost-model ranking plus a short
+    timed run of the best candidates), forced to the fused build it found."""
+    plan = eb.Plan(ndim, dims, shape, r, c, dtype, eb.DIRICHLET)
+    ws = plan.workspace()
+    plan.tune(x, torch.empty_like(x), tune_steps, ws, max_candidates=candidates)
+    if plan.params().variant == 1:
+        plan.set_params(variant=plan.params().fused_variant)
+    return plan, ws
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+@pytest.mark.parametrize("shape,r", [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2)])
+def test_2d_fullsize_blocked_equals_naive(shape, r, dtype):
+    """The whole 8192^2 grid after 1000 steps, in the benchmark's launch
+    configuration, equals the one-step-per-launch kernel bit for bit
+    (Section 4.1: tiling reorders the updates without changing them); for
+    FP32 storage, the oracle's corner windows of the same run (the values
+    the device holds, FP32-rounded coefficients) within 1e-5."""
+    eb = _eb()
+    dims, steps = (8192, 8192), 1000
+    g, c = synth.problem(2, dims, shape, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED + 17 * r + shape)
+    x = torch.from_numpy(g).to(eb.torch_dtype(dtype)).cuda()
+    plan, ws = bench_tuned_plan(eb, 2, dims, shape, r, c, x, dtype, 48, 16)
+    y = torch.empty_like(x)
+    plan.run(x, y, steps, ws)
+    assert plan.sync(ws) == 0
+    yn = torch.empty_like(x)
+    plan.run(x, yn, steps, ws, naive=True)
+    assert plan.sync(ws) == 0
+    assert torch.equal(y, yn), f"params {plan.params().as_dict()}"
+    if dtype == eb.F32:
+        held = x.double().cpu().numpy()
+        c_held = c.astype(np.float32).astype(np.float64)
+        out = y.double().cpu().numpy()
+        assert corner_check(held, out, shape, r, c_held, steps, 6, high=False) <= 1e-5
+        assert corner_check(held, out, shape, r, c_held, steps, 6, high=True) <= 1e-5
+
+
+@pytest.mark.parametrize("shape,r", [(0, 1), (0, 2), (1, 1), (1, 2)])
+def test_3d_fullsize_blocked_equals_naive(shape, r):
+    """The whole 512^3 FP64 grid after 200 steps, in the benchmark's tuned
+    launch configuration, equals the one-step-per-launch kernel bit for bit."""
+    eb = _eb()
+    dims, steps = (512, 512, 512), 200
+    g, c = synth.problem(3, dims, shape, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED + 31 * r + shape)
+    x = torch.from_numpy(g).cuda()
+    del g
+    plan, ws = bench_tuned_plan(eb, 3, dims, shape, r, c, x, eb.F64, 8, 4)
+    y = torch.empty_like(x)
+    plan.run(x, y, steps, ws)
+    assert plan.sync(ws) == 0
+    yn = torch.empty_like(x)
+    plan.run(x, yn, steps, ws, naive=True)
+    assert plan.sync(ws) == 0
+    assert torch.equal(y, yn), f"params {plan.params().as_dict()}"
