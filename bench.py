@@ -14,6 +14,7 @@ replicas only -- each rank solves its own copy of the set (weak scaling).
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -403,73 +404,152 @@ def npoints3(shape, r):
     return 6 * r + 1 if shape == 0 else (2 * r + 1) ** 3
 
 
-def run_batch(args):
+def apply_params(ebisu, plan, q):
+    """Give `plan` the tuned parameters `q` of another plan of the same
+    stencil and storage (the fused build the tuner found); False if they do
+    not fit this grid."""
+    try:
+        if q.fused_variant == 2:
+            plan.set_params(variant=2, depth=q.depth, tile_s=q.tile_s, ctas_per_sm=q.ctas_per_sm)
+        else:
+            plan.set_params(variant=0, tile_x=q.tile_x, tile_y=q.tile_y, tile_s=q.tile_s, depth=q.depth,
+                            ctas_per_sm=q.ctas_per_sm)
+        return True
+    except ebisu.EbisuError:
+        return False
+
+
+BATCH_FORMS = [("f64", 0, None), ("f32", 1, None), ("bf16", 2, None), ("bf16-sr", 2, "sr")]
+
+
+def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
     """512 uneven 2D 9-point box grids (sides log-uniform in [256, 4096],
-    aspect in [0.25, 4], 16-512 steps) in one persistent launch per dtype,
-    against the same grids run one after another with ebisu_run."""
+    aspect in [0.25, 4], 16-512 steps) in one persistent launch per storage
+    form.  The autotuner picks tiles and depth per shape bucket (sides
+    rounded to half powers of two): the bucket's first grid is tuned, the
+    others take its parameters.  The error of each form is checked against
+    the oracle on the sampled grids small enough for it (whole grids), and
+    optionally the same grids are timed one launch each."""
     import numpy as np
     import torch
     from paper_2305_07390_gb300 import ebisu, synth
-    mix = synth.batch_mix(512)
-    out = {"workload": "batch: 512 uneven 2D 9-point box grids, Dirichlet; each plan's default parameters (FP64: "
-                       "the cost model's shared-memory tiles and depth; FP32/BF16: the register-streaming build "
-                       "at its preferred depth)", "n_grids": len(mix), "cells": int(sum(a * b for a, b, _ in mix)),
-           "cell_updates": int(sum(a * b * s for a, b, s in mix)), "by_dtype": {}}
+    mix = synth.batch_mix(count)
+    cells = int(sum(a * b for a, b, _ in mix))
+    updates = int(sum(a * b * s for a, b, s in mix))
+    out = {"workload": f"batch: {count} uneven 2D 9-point box grids (sides log-uniform in [256, 4096], aspect "
+                       "[0.25, 4]), 16-512 steps each, Dirichlet, one persistent launch per storage form; tiles "
+                       "and depth from the autotuner per shape bucket", "n_grids": len(mix), "cells": cells,
+           "cell_updates": updates, "by_form": {}}
+    # the grids the oracle checks: the smallest ones, whole
+    order = sorted(range(len(mix)), key=lambda i: mix[i][0] * mix[i][1])
+    sample = sorted(order[:6]) if check else []
+    refs = {}
+    if check:
+        import oracle
+        for i in sample:
+            ny, nx, st = mix[i]
+            g, c = synth.problem(2, (ny, nx), synth.BOX, 1, synth.DIRICHLET, seed=synth.DEFAULT_SEED + i)
+            for fname, dt, _ in BATCH_FORMS:
+                held = torch.from_numpy(g).to(ebisu.torch_dtype(dt)).double().numpy()
+                ch = c if dt == 0 else c.astype(np.float32).astype(np.float64)
+                refs[(fname, i)] = oracle.run(held, synth.BOX, 1, ch, synth.DIRICHLET, st,
+                                              nthreads=os.cpu_count())
     stream = torch.cuda.current_stream()
-    for dname, dt in (("f64", ebisu.F64), ("f32", ebisu.F32), ("bf16", ebisu.BF16)):
-        plans, xs, ys, steps = [], [], [], []
+    for fname, dt, rounding in BATCH_FORMS:
+        plans, xs, ys, steps_l = [], [], [], []
+        tuned = {}
+        t0 = time.perf_counter()
         for i, (ny, nx, st) in enumerate(mix):
             g, c = synth.problem(2, (ny, nx), synth.BOX, 1, synth.DIRICHLET, seed=synth.DEFAULT_SEED + i)
-            plans.append(ebisu.Plan(2, (ny, nx), ebisu.BOX, 1, c, dt, ebisu.DIRICHLET))
-            xs.append(torch.from_numpy(g).to(ebisu.torch_dtype(dt)).cuda())
-            ys.append(torch.empty_like(xs[-1]))
-            steps.append(st)
-        ws = torch.empty(ebisu.batch_workspace_bytes(plans, steps), dtype=torch.uint8, device="cuda")
-        b = ebisu.Batch(plans, xs, ys, steps, ws)
-        for _ in range(args.warmup):
+            plan = ebisu.Plan(2, (ny, nx), ebisu.BOX, 1, c, dt, ebisu.DIRICHLET)
+            if rounding == "sr":
+                plan.set_rounding(ebisu.ROUND_STOCHASTIC, synth.DEFAULT_SEED)
+            x = torch.from_numpy(g).to(ebisu.torch_dtype(dt)).cuda()
+            y = torch.empty_like(x)
+            key = (round(2 * math.log2(ny)), round(2 * math.log2(nx)))
+            if key not in tuned:
+                ws = plan.workspace()
+                plan.tune(x, y, 32, ws, max_candidates=6)
+                tuned[key] = plan.params()
+                del ws
+            elif not apply_params(ebisu, plan, tuned[key]):
+                pass  # keeps the defaults
+            plans.append(plan)
+            xs.append(x)
+            ys.append(y)
+            steps_l.append(st)
+        t_tune = time.perf_counter() - t0
+        ws = torch.empty(ebisu.batch_workspace_bytes(plans, steps_l), dtype=torch.uint8, device="cuda")
+        b = ebisu.Batch(plans, xs, ys, steps_l, ws)
+        for _ in range(warmup):
             b.launch()
         torch.cuda.synchronize()
         assert b.sync() == 0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             b.launch()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms_batch = e0.elapsed_time(e1) / args.steps
-        # the same grids one after another (one launch each)
-        wss = [p.workspace() for p in plans[:1]]
-        big = max(p.workspace_bytes() for p in plans)
-        wsa = torch.empty(big, dtype=torch.uint8, device="cuda")
-        e0.record(stream)
-        for p, x, y, st in zip(plans, xs, ys, steps):
-            p.run(x, y, st, wsa)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms_alone = e0.elapsed_time(e1)
-        out["by_dtype"][dname] = {"ms_batched": ms_batch, "ms_one_by_one": ms_alone,
-                                  "cell_updates_per_s": out["cell_updates"] / (ms_batch * 1e-3),
-                                  "batching_speedup": ms_alone / ms_batch}
-        del plans, xs, ys, ws, b, wsa
+        assert b.sync() == 0
+        ms_batch = e0.elapsed_time(e1) / steps
+        row = {"ms_batched": ms_batch, "cell_updates_per_s": updates / (ms_batch * 1e-3),
+               "rounding": "stochastic" if rounding == "sr" else "nearest even",
+               "buckets_tuned": len(tuned), "tuning_s": t_tune,
+               "kernels": sorted({"rs_kernel" if (p.params().variant == 2 or p.params().fused_variant == 2)
+                                  else "tb_kernel" for p in plans})}
+        if check:
+            errs = []
+            for i in sample:
+                ref = refs[(fname, i)]
+                dev = ys[i].double().cpu().numpy()
+                errs.append(float(np.max(np.abs(dev[1:-1, 1:-1] - ref[1:-1, 1:-1])) /
+                                  np.max(np.abs(ref[1:-1, 1:-1]))))
+            row["rel_linf_vs_oracle_max"] = max(errs)
+            row["oracle_sample"] = (f"{len(sample)} whole grids (the smallest of the mix, "
+                                    f"{min(mix[i][0] * mix[i][1] for i in sample)}-"
+                                    f"{max(mix[i][0] * mix[i][1] for i in sample)} cells, "
+                                    f"{min(mix[i][2] for i in sample)}-{max(mix[i][2] for i in sample)} steps)")
+        if one_by_one:
+            big = max(p.workspace_bytes() for p in plans)
+            wsa = torch.empty(big, dtype=torch.uint8, device="cuda")
+            e0.record(stream)
+            for p, x, y, st in zip(plans, xs, ys, steps_l):
+                p.run(x, y, st, wsa)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            row["ms_one_by_one"] = e0.elapsed_time(e1)
+            row["batching_speedup"] = row["ms_one_by_one"] / ms_batch
+            del wsa
+        out["by_form"][fname] = row
+        del plans, xs, ys, ws, b
         torch.cuda.empty_cache()
-    f64 = out["by_dtype"]["f64"]["ms_batched"]
-    for dname in ("f32", "bf16"):
-        out["by_dtype"][dname]["speedup_vs_f64"] = f64 / out["by_dtype"][dname]["ms_batched"]
-    print(json.dumps(out), flush=True)
+    f64 = out["by_form"]["f64"]["ms_batched"]
+    for fname, _, _ in BATCH_FORMS[1:]:
+        out["by_form"][fname]["speedup_vs_f64"] = f64 / out["by_form"][fname]["ms_batched"]
+    return out
 
 
-def run_serve(args):
+def run_batch(args):
+    """The batch workload alone (see batch_leg), with one-by-one timings."""
+    print(json.dumps(batch_leg(args.warmup, args.steps, one_by_one=True)), flush=True)
+
+
+def serve_leg(rates, seconds, max_slots=0, order=None, max_wait_s=2.0, queue_limit=256):
     """Open-loop Poisson arrivals through the serving loop (continuous
-    batching, 120 GB budget).  Inputs are prefixes of one preallocated buffer
-    per (ndim, dtype) and outputs share one buffer per (ndim, dtype): results
-    are not kept (their correctness is covered by the test suite); this
-    measures admission, queueing and latency."""
+    batching, 120 GB budget, lanes scaled with the budget, least estimated
+    work first, requests refused once the queued work exceeds max_wait_s).
+    Inputs are prefixes of one preallocated buffer per (ndim, dtype) and
+    outputs share one buffer per (ndim, dtype): results are not kept (their
+    correctness is covered by the test suite); this measures admission,
+    queueing and latency."""
     import numpy as np
     import torch
     from paper_2305_07390_gb300 import ebisu, synth
     budget = 120 << 30
-    srv = ebisu.Server(hbm_budget=budget, max_slots=4)
-    srv.set_max_queue(256)
+    srv = ebisu.Server(hbm_budget=budget, max_slots=max_slots)
+    srv.set_max_queue(queue_limit)
+    srv.set_policy(ebisu.SERVE_SHORTEST if order is None else order, max_wait_s)
     bufs = {}
     for nd, side in ((2, 8192 + 2), (3, 512 + 2)):
         for dname, dt in (("f64", ebisu.F64), ("f32", ebisu.F32)):
@@ -478,8 +558,8 @@ def run_serve(args):
             bufs[(nd, dname)] = (x, torch.empty_like(x))
     coef = {}
     results = []
-    for rate in [float(v) for v in args.serve_rates.split(",")]:
-        reqs = synth.serve_mix(rate, args.serve_seconds)
+    for rate in rates:
+        reqs = synth.serve_mix(rate, seconds)
         tickets = []
         rejected = 0
         t0 = time.perf_counter()
@@ -507,16 +587,22 @@ def run_serve(args):
         lat.sort()
         q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
         st = srv.stats()
-        results.append({"rate_hz": rate, "offered": len(reqs), "completed": len(tickets), "rejected": rejected,
+        results.append({"rate_hz": rate, "offered": len(reqs), "arrival_rate_hz": len(reqs) / t_arrive,
+                        "completed": len(tickets), "rejected": rejected,
                         "p50_s": q(0.50), "p99_s": q(0.99), "max_s": lat[-1] if lat else None,
                         "throughput_cell_updates_per_s": upd / t_all, "arrival_window_s": t_arrive,
                         "drain_s": t_all - t_arrive, "peak_bytes": st["peak_bytes"]})
-        print(json.dumps(results[-1]), flush=True)
+        print(json.dumps(results[-1]), file=sys.stderr, flush=True)
     srv.close()
-    print(json.dumps({"workload": "serve: Poisson arrivals, 50% 2D (256^2-8192^2, 5pt star / 9pt box), 50% 3D "
-                                  "(64^3-512^3, 7pt star / 27pt box), FP64/FP32, 10-1000 steps, 120 GB budget, "
-                                  "queue limit 256, 4 lanes", "seconds_per_rate": args.serve_seconds,
-                      "rates": results}), flush=True)
+    return {"workload": "serve: Poisson arrivals, 50% 2D (256^2-8192^2, 5pt star / 9pt box), 50% 3D (64^3-512^3, "
+                        "7pt star / 27pt box), FP64/FP32 50/50, 10-1000 steps, 120 GB budget, lanes scaled with "
+                        f"the budget, least estimated work first, queued-work limit {max_wait_s} s, queue limit "
+                        f"{queue_limit}", "seconds_per_rate": seconds, "rates": results}
+
+
+def run_serve(args):
+    rates = [float(v) for v in args.serve_rates.split(",")]
+    print(json.dumps(serve_leg(rates, args.serve_seconds)), flush=True)
 
 
 def cpu_baseline(budget_s=15.0):
@@ -602,7 +688,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ebisu", choices=["ebisu", "reference"])
     ap.add_argument("--solve-steps", type=int, default=SOLVE_STEPS)
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg (and the oracle checks)")
+    ap.add_argument("--no-legs", action="store_true", help="skip the batch and serve legs of the default run")
     ap.add_argument("--tune", type=int, default=16, help="candidates the autotuner times per stencil")
     ap.add_argument("--case", default=None,
                     help="profiling case: run one solve of 'DIM:SHAPE:R' (e.g. 2:box:2) and exit")
@@ -762,7 +849,7 @@ def main():
     h2d = sum(p["host_in"].numel() * 8 for p in probs)
     d2h = sum(p["host_out"].numel() * 8 for p in probs)
     barrier()
-    for _ in range(args.steps):
+    for _ in range(min(args.steps, 3)):  # the slowest of up to three end-to-end steps
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -781,6 +868,25 @@ def main():
     # and against the FP64 GPU result (whole grid, original coefficients)
     forms = []
     hbm, hbm_src = hbm_peak()
+    ref64 = {}  # FP64 solves of the rounded inputs with FP32-rounded coefficients
+
+    def same_problem_fp64(p, dt, xl):
+        """The FP64 path (pinned to the oracle at 1e-12) on exactly the
+        problem the reduced form solves: its stored input and its FP32-rounded
+        coefficients; cached per input rounding and stencil."""
+        key = (ebisu.torch_dtype(dt), p["name"])
+        if key not in ref64:
+            c32 = [float(np.float32(v)) for v in p["plan"].coeffs]
+            pl = ebisu.Plan(2, (N, N), p["shape"], p["r"], c32, ebisu.F64, ebisu.DIRICHLET)
+            apply_params(ebisu, pl, p["plan"].params())
+            x64 = xl.double()
+            y64 = torch.empty_like(x64)
+            pl.run(x64, y64, steps, p["ws"], stream=sh)
+            assert pl.sync(p["ws"]) == 0
+            ref64[key] = y64
+            del x64
+        return ref64[key]
+
     for dname, dt, rounding in forms_dt:
         rows = []
         es = 4 if dt == ebisu.F32 else 2
@@ -808,6 +914,8 @@ def main():
             rr = p["r"]
             ref = p["y"][rr:-rr, rr:-rr]
             err = float((yl[rr:-rr, rr:-rr].double() - ref).abs().max() / ref.abs().max())
+            ref_s = same_problem_fp64(p, dt, xl)[rr:-rr, rr:-rr]
+            err_s = float((yl[rr:-rr, rr:-rr].double() - ref_s).abs().max() / ref_s.abs().max())
             win = yl[rr:rr + OracleCones.W, rr:rr + OracleCones.W].double().cpu().numpy()
             a.record(stream)
             plan.run(xl, yl, min(steps, 100), wsl, stream=sh, naive=True)
@@ -819,7 +927,8 @@ def main():
             rows.append(dict(stencil=p["name"], cell_updates_per_s=rate,
                              speedup_vs_fp64=rate / d["cell_updates_per_s"],
                              naive_cell_updates_per_s=naive_rate, speedup_vs_naive=rate / naive_rate,
-                             rel_linf_vs_fp64=err, tuner_preferred=VARIANT_NAMES[tuned],
+                             rel_linf_vs_fp64=err, rel_linf_vs_fp64_same_problem=err_s,
+                             tuner_preferred=VARIANT_NAMES[tuned],
                              kernel=kernel_name(plan), params=prm,
                              roofline=stencil_roofline(rate, p["P"], es, prm["depth"], probe["f32_flops"], hbm)))
             rows[-1]["_win"] = win
@@ -831,6 +940,8 @@ def main():
                           sum(cells * steps / r_["cell_updates_per_s"] for r_ in rows),
                           roofline_peaks={"hbm_bytes_per_s": hbm, "hbm_source": hbm_src,
                                           "fp32_flops": probe["f32_flops"], "fp32_source": "live probe (FMA loop)"}))
+    del ref64
+    torch.cuda.empty_cache()
     cone_refs = cones.join() if cones is not None else {}
     for f in forms:
         for r_ in f["per_stencil"]:
@@ -838,9 +949,21 @@ def main():
             ref = cone_refs.get((f["dtype"], r_["stencil"]))
             r_["rel_linf_vs_oracle"] = (None if ref is None else
                                         float(np.max(np.abs(win - ref)) / np.max(np.abs(ref))))
-        f["oracle_check"] = (f"corner window {OracleCones.W}x{OracleCones.W} of each {N}x{N} solve after "
-                             f"{steps} steps; oracle in FP64 on the stored (rounded) input and the "
-                             "FP32-rounded coefficients, over the window's dependency cone")
+        f["oracle_check"] = (f"rel_linf_vs_oracle: corner window {OracleCones.W}x{OracleCones.W} of each "
+                             f"{N}x{N} solve after {steps} steps, the oracle in FP64 on the stored (rounded) "
+                             "input and the FP32-rounded coefficients over the window's dependency cone; "
+                             "rel_linf_vs_fp64_same_problem: the whole grid against the FP64 path (equal to "
+                             "the oracle within 1e-12 in the parity tests) on that same input and "
+                             "coefficients; rel_linf_vs_fp64: the whole grid against the FP64 solve with the "
+                             "original coefficients (adds the coefficients' rounding)")
+    # the batched form (C4) and the serving loop (C5), short legs
+    for p in probs:
+        del p["x"], p["y"], p["ws"]
+    torch.cuda.empty_cache()
+    batch = serve = None
+    if not args.no_legs:
+        batch = batch_leg(1, 1, check=(rank == 0 and not args.no_cpu))
+        serve = serve_leg([10.0, 200.0, 2000.0], 5.0)
     cpu = None
     if rank == 0 and not args.no_cpu and ws_n == 1:
         cpu = cpu_baseline()
@@ -859,6 +982,8 @@ def main():
                          **peak_info),
         "per_stencil": per,
         "precision_forms": forms,
+        "batch": batch,
+        "serve": serve,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": max(e2e_ms)},
         "gpu_launches": len(probs) * args.steps,  # one persistent launch per solve

@@ -367,7 +367,10 @@ int ebisu_batch_destroy(ebisu_batch_t batch);
 /* Serving loop (continuous batching, host thread + CUDA streams).
  *   hbm_budget : bytes of device memory the server may hold for grids and
  *                workspaces; requests are admitted while they fit.
- *   max_slots  : requests that may run on the device at once.
+ *   max_slots  : launches (lanes) that may run on the device at once, 1..64;
+ *                0 = scale with the budget (one per 4 GiB, 4 to 32).  Each
+ *                lane runs one batched launch of the requests admitted
+ *                together.
  * The server allocates and frees its own device memory inside the budget. */
 int ebisu_serve_create(size_t hbm_budget, int max_slots, ebisu_server_t* out);
 
@@ -397,6 +400,20 @@ int ebisu_serve_stats(ebisu_server_t s, int64_t* stats);
 
 /* Admission control: most requests that may wait in the queue (>= 1). */
 int ebisu_serve_set_max_queue(ebisu_server_t s, int max_queue);
+
+/* Scheduling and admission policy (not in the paper; serving only).
+ *   order      : EBISU_SERVE_FIFO (arrival order, the default) or
+ *                EBISU_SERVE_SHORTEST: least estimated work first, the
+ *                estimate being the request's cell updates over half its
+ *                stencil's roofline (HBM over 2S/t bytes, FMA rate over 2P
+ *                flops) for its storage type and depth; a request's priority
+ *                is that estimate minus the time it has already waited, so
+ *                large requests are delayed, never starved.
+ *   max_wait_s : > 0 = admission control on predicted delay: a request is
+ *                refused (EBISU_ERR_BUSY) when the estimated work already
+ *                queued exceeds max_wait_s seconds; 0 = off (the default). */
+enum ebisu_serve_order { EBISU_SERVE_FIFO = 0, EBISU_SERVE_SHORTEST = 1 };
+int ebisu_serve_set_policy(ebisu_server_t s, int order, double max_wait_s);
 
 /* Cancel a request that has not started (EBISU_ERR_NOT_READY if it has). */
 int ebisu_serve_cancel(ebisu_server_t s, uint64_t ticket);

@@ -33,7 +33,7 @@ int scratch_address(void** out)
 {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return ebisu::fail_cuda(e);
+    if (e != cudaSuccess) return fail_cuda(e);
     if (!p) return EBISU_ERR_CUDA;
     *out = p;
     return EBISU_OK;

@@ -19,9 +19,12 @@ void set_cuda_error(cudaError_t e)
     snprintf(g_err, sizeof(g_err), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
 }
 
-int fail_cuda(cudaError_t e)
+int fail_cuda_at(cudaError_t e, const char* file, int line)
 {
-    set_cuda_error(e);
+    const char* base = strrchr(file, '/');
+    snprintf(g_err, sizeof(g_err), "%s:%d: %s: %s", base ? base + 1 : file, line, cudaGetErrorName(e),
+             cudaGetErrorString(e));
+    cudaGetLastError();
     return EBISU_ERR_CUDA;
 }
 

@@ -63,7 +63,11 @@ const DeviceInfo& device_rates();
 void record_device_rates(const double* probe_out);
 
 void set_cuda_error(cudaError_t e);
-int fail_cuda(cudaError_t e);
+// Record a failed CUDA call (its error and the source line that saw it, for
+// ebisu_last_cuda_error), clear the runtime's last-error state so the
+// caller's next CUDA call does not report it again, and return EBISU_ERR_CUDA.
+int fail_cuda_at(cudaError_t e, const char* file, int line);
+#define fail_cuda(e) ::ebisu::fail_cuda_at((e), __FILE__, __LINE__)
 
 int ring_q(int radius);   // slots of a level-1.. ring (2r+2)
 int ring_q0(int radius, int ndim, int variant, size_t esize);  // input ring slots (2r+1+prefetch)

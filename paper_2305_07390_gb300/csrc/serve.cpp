@@ -4,8 +4,11 @@
 // queued at submit time; on every tick the scheduler
 //   1. retires finished launches (event query), frees their device memory and
 //      returns their bytes to the HBM budget;
-//   2. admits queued requests in arrival order while the budget allows and a
-//      lane is free (a request that can never fit is refused at submit);
+//   2. admits queued requests while the budget allows and a lane is free (a
+//      request that can never fit is refused at submit), in arrival order or
+//      -- ebisu_serve_set_policy -- least estimated work first, where a
+//      request's priority is its estimated run time minus the time it has
+//      waited (so a large request is not passed over forever);
 //   3. groups the newly admitted requests by kernel type and starts each group
 //      as ONE batched persistent launch (ebisu_batch_*) on a free lane: the
 //      request's grid is copied into server memory (kept resident until the
@@ -43,6 +46,7 @@ struct Request {
     void* out = nullptr;
     int64_t steps = 0;
     size_t need = 0;
+    double est_s = 0;  // estimated run time alone on the GPU
     double t_submit = 0, t_done = 0;
     int state = 0;  // 0 queued, 1 running, 2 done, 3 cancelled, 4 failed
     int status = EBISU_OK;
@@ -60,12 +64,30 @@ struct Launch {
 
 constexpr size_t kDefaultMaxQueue = 1024;
 
+// Estimated run time of a request alone on the GPU: cell updates over half
+// the roofline of its stencil and storage type at its temporal depth (the
+// lower of HBM bandwidth over 2S/t bytes per update and the FMA rate over 2P
+// flops).  Only used to order requests and to predict queue waits.
+double estimate_s(const ebisu_plan_s* p, int64_t steps)
+{
+    const DeviceInfo& dv = device_rates();
+    const double t = std::max(1, p->prm.variant == 1 ? 1 : p->prm.depth);
+    const double hbm = 6.7e12 / (2.0 * (double)p->esize / t);
+    const double fp = (p->dtype == EBISU_F64 ? dv.f64 : dv.f32) / (2.0 * p->npts);
+    const double rate = 0.5 * std::min(hbm, fp);
+    const double cells = (double)p->n[0] * p->n[1] * p->n[2];
+    return cells * (double)steps / rate;
+}
+
 }  // namespace
 
 struct ebisu_server_s {
     size_t budget = 0;
     int max_slots = 1;
     size_t max_queue = kDefaultMaxQueue;
+    int order = EBISU_SERVE_FIFO;
+    double max_wait_s = 0;  // admission control: refuse when the predicted wait exceeds it (0 = off)
+    double queued_est = 0;  // estimated work of the queued requests (s)
     int device = 0;
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
@@ -210,14 +232,34 @@ struct ebisu_server_s {
                 std::vector<Request*> admitted;
                 int free_lanes = 0;
                 for (int b : lane_busy) free_lanes += (b == 0);
+                const double tnow = now_s();
                 while (!queue.empty() && free_lanes > 0) {
-                    Request* r = queue.front();
+                    // the next request: the queue's head, or the one with the
+                    // least estimated run time net of its wait so far
+                    auto pick = queue.begin();
+                    if (order == EBISU_SERVE_SHORTEST) {
+                        double best = 1e300;
+                        for (auto q = queue.begin(); q != queue.end(); ++q) {
+                            if ((*q)->state == 3) {  // cancelled: remove it first
+                                pick = q;
+                                break;
+                            }
+                            const double key = (*q)->est_s - (tnow - (*q)->t_submit);
+                            if (key < best) {
+                                best = key;
+                                pick = q;
+                            }
+                        }
+                    }
+                    Request* r = *pick;
                     if (r->state == 3) {  // cancelled while queued
-                        queue.pop_front();
+                        queued_est -= r->est_s;
+                        queue.erase(pick);
                         continue;
                     }
                     if (held + r->need > budget) break;
-                    queue.pop_front();
+                    queue.erase(pick);
+                    queued_est -= r->est_s;
                     r->state = 1;
                     held += r->need;
                     peak = std::max(peak, held);
@@ -247,6 +289,7 @@ struct ebisu_server_s {
                             (*it)->state = 0;
                             held -= (*it)->need;
                             --nrunning;
+                            queued_est += (*it)->est_s;
                             queue.push_front(*it);
                         }
                         continue;
@@ -271,8 +314,10 @@ extern "C" {
 
 int ebisu_serve_create(size_t hbm_budget, int max_slots, ebisu_server_t* out)
 {
-    if (!out || hbm_budget == 0 || max_slots < 1 || max_slots > 64) return EBISU_ERR_INVALID_ARG;
+    if (!out || hbm_budget == 0 || max_slots < 0 || max_slots > 64) return EBISU_ERR_INVALID_ARG;
     *out = nullptr;
+    // 0: lanes scale with the budget, one per 4 GiB, 4 to 32
+    if (max_slots == 0) max_slots = (int)std::min<size_t>(32, std::max<size_t>(4, hbm_budget >> 32));
     ebisu_server_s* s = new (std::nothrow) ebisu_server_s();
     if (!s) return EBISU_ERR_OOM;
     s->budget = hbm_budget;
@@ -305,6 +350,7 @@ int ebisu_serve_submit(ebisu_server_t s, ebisu_plan_t plan, const void* in_dev, 
     r->out = out_dev;
     r->steps = steps;
     r->need = ebisu_server_s::need_of(plan, steps);
+    r->est_s = estimate_s(plan, steps);
     r->t_submit = now_s();
     std::lock_guard<std::mutex> lk(s->mu);
     ++s->submitted;
@@ -313,11 +359,15 @@ int ebisu_serve_submit(ebisu_server_t s, ebisu_plan_t plan, const void* in_dev, 
         delete r;
         return EBISU_ERR_BUDGET;
     }
-    if (s->queue.size() >= s->max_queue || s->stop) {
+    // admission control: the queue's length limit, and (if set) the predicted
+    // wait -- the estimated work already queued -- against the wait limit
+    const bool late = s->max_wait_s > 0 && s->queued_est > s->max_wait_s;
+    if (s->queue.size() >= s->max_queue || s->stop || late) {
         ++s->rejected;
         delete r;
         return EBISU_ERR_BUSY;
     }
+    s->queued_est += r->est_s;
     r->id = s->next_id++;
     s->reqs[r->id] = r;
     s->queue.push_back(r);
@@ -375,6 +425,17 @@ int ebisu_serve_set_max_queue(ebisu_server_t s, int max_queue)
     return EBISU_OK;
 }
 
+int ebisu_serve_set_policy(ebisu_server_t s, int order, double max_wait_s)
+{
+    if (!s || (order != EBISU_SERVE_FIFO && order != EBISU_SERVE_SHORTEST) || !(max_wait_s >= 0))
+        return EBISU_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->order = order;
+    s->max_wait_s = max_wait_s;
+    s->cv_sched.notify_all();
+    return EBISU_OK;
+}
+
 int ebisu_serve_cancel(ebisu_server_t s, uint64_t ticket)
 {
     if (!s) return EBISU_ERR_INVALID_ARG;
@@ -384,6 +445,8 @@ int ebisu_serve_cancel(ebisu_server_t s, uint64_t ticket)
     Request* r = it->second;
     if (r->state != 0) return EBISU_ERR_NOT_READY;
     r->state = 3;
+    s->queued_est -= r->est_s;  // it no longer delays later requests
+    r->est_s = 0;
     r->t_done = now_s();
     s->cv_done.notify_all();
     return EBISU_OK;

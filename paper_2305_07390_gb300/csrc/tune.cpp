@@ -235,8 +235,17 @@ int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, dou
                     for (int waves : {1, 2, 4}) {
                         int64_t nts = std::max<int64_t>(1, (ctas * waves + nt2 * nt1 - 1) / (nt2 * nt1));
                         nts = std::min<int64_t>(nts, p->n[0]);
+                        // grids smaller than a wave: fewer, taller tiles (a
+                        // band shorter than 2rt rows is all overlap)
+                        const int64_t smin = std::max(4, 2 * p->radius * d);
+                        if ((p->n[0] + nts - 1) / nts < smin) nts = std::max<int64_t>(1, p->n[0] / smin);
                         q.tile_s = (int)((p->n[0] + nts - 1) / nts);
-                        if (q.tile_s < std::max(4, 2 * p->radius * d) && nts > 1) continue;
+                        bool dup = false;  // several wave counts can give the same band
+                        for (const auto& c : cand)
+                            dup = dup || (c.second.tile_x == q.tile_x && c.second.tile_y == q.tile_y &&
+                                          c.second.tile_s == q.tile_s && c.second.depth == q.depth &&
+                                          c.second.ctas_per_sm == q.ctas_per_sm);
+                        if (dup) continue;
                         const double pp = model_pp(p, q, steps, nullptr, nullptr);
                         cand.push_back({pp, q});
                     }
@@ -305,19 +314,14 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
     if (in == out) return EBISU_ERR_INVALID_ARG;
     std::vector<ebisu_params> cand(max_candidates);
     std::vector<double> pred(max_candidates);
-    int n = rank_candidates(plan, steps, cand.data(), pred.data(), max_candidates);
-    if (n < 1) return EBISU_ERR_UNSUPPORTED;
-    ebisu_params naive = cand[0];
-    naive.variant = 1;
     const bool sr = plan_sr(plan);
-    if (sr) {
-        // stochastic rounding: no shared-memory build; the one-step kernel
-        // keeps the plan's current fused parameters
-        n = 0;
-        cand.clear();
-        naive = plan->prm;
-        naive.variant = 1;
-    }
+    int n = sr ? 0 : rank_candidates(plan, steps, cand.data(), pred.data(), max_candidates);
+    if (n < 1 && !sr) return EBISU_ERR_UNSUPPORTED;
+    cand.resize(n);  // the ranking may return fewer than max_candidates
+    // (stochastic rounding: no shared-memory build; the one-step kernel keeps
+    // the plan's current fused parameters)
+    ebisu_params naive = sr ? plan->prm : cand[0];
+    naive.variant = 1;
     // The one-step-per-launch kernel is timed too: where the fused kernel
     // cannot beat it (measured: 3D low-order FP64 stars), the plan runs it.
     cand.push_back(naive);

@@ -24,6 +24,7 @@ STAR, BOX = 0, 1
 F64, F32, BF16 = 0, 1, 2
 DIRICHLET, PERIODIC = 0, 1
 ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1
+SERVE_FIFO, SERVE_SHORTEST = 0, 1
 
 
 class EbisuError(RuntimeError):
@@ -105,6 +106,7 @@ SIGNATURES = {
     "ebisu_serve_stats": (_I, [_P, ctypes.POINTER(_I64)]),
     "ebisu_serve_cancel": (_I, [_P, ctypes.c_uint64]),
     "ebisu_serve_set_max_queue": (_I, [_P, _I]),
+    "ebisu_serve_set_policy": (_I, [_P, _I, _D]),
     "ebisu_serve_destroy": (_I, [_P]),
     "ebisu_probe_device": (_I, [ctypes.POINTER(_D)]),
 }
@@ -416,6 +418,9 @@ class Server:
 
     def set_max_queue(self, n: int):
         _check(lib().ebisu_serve_set_max_queue(self.h, int(n)), "ebisu_serve_set_max_queue")
+
+    def set_policy(self, order: int, max_wait_s: float = 0.0):
+        _check(lib().ebisu_serve_set_policy(self.h, int(order), float(max_wait_s)), "ebisu_serve_set_policy")
 
     def cancel(self, ticket) -> int:
         return int(lib().ebisu_serve_cancel(self.h, ctypes.c_uint64(ticket)))

@@ -226,3 +226,35 @@ def test_serve_budget_admission_and_rejection():
     assert rc == eb.ERR_BUDGET
     assert srv.stats()["rejected"] == 1
     srv.close()
+
+
+def test_serve_shortest_first_and_wait_limit():
+    """Least-estimated-work-first ordering lets small requests that arrive
+    behind large ones finish first; results still equal each problem alone.
+    The wait limit refuses requests once the queued work exceeds it."""
+    eb = _eb()
+    big = make_problem(eb, 2, (4096, 4096), 1, 2, eb.F64, 0, 21)          # ~1.7e10 updates
+    smalls = [make_problem(eb, 2, (300, 400), 0, 1, eb.F32, 0, 30 + i) for i in range(6)]
+    srv = eb.Server(hbm_budget=16 << 30, max_slots=1)  # one lane: the order is the schedule
+    srv.set_policy(eb.SERVE_SHORTEST)
+    yb = [torch.empty_like(big[1]) for _ in range(3)]
+    ys = [torch.empty_like(s[1]) for s in smalls]
+    tb = [srv.submit(big[0], big[1], y, 1000) for y in yb]
+    ts = [srv.submit(s[0], s[1], y, 50) for s, y in zip(smalls, ys)]
+    lat_b = [srv.wait(t, timeout_s=300) for t in tb]
+    lat_s = [srv.wait(t, timeout_s=300) for t in ts]
+    # the first large request may already be running; the small ones overtake the rest
+    assert max(lat_s) < max(lat_b)
+    ref_b = alone(big[0], big[1], 1000)
+    assert all(torch.equal(y, ref_b) for y in yb)
+    for s, y in zip(smalls, ys):
+        assert torch.equal(y, alone(s[0], s[1], 50))
+    # admission control on predicted wait: with a tiny limit, a queue of large
+    # requests turns further submissions away
+    srv.set_policy(eb.SERVE_FIFO, max_wait_s=1e-3)
+    rcs = [srv.try_submit(big[0], big[1], yb[i % 3], 1000)[0] for i in range(4)]
+    assert eb.ERR_BUSY in rcs
+    for rc in rcs:
+        assert rc in (eb.OK, eb.ERR_BUSY)
+    srv.close()
+    assert srv.h is None

@@ -273,3 +273,21 @@ def test_rs3t_in_place_and_timeout(monkeypatch):
     assert plan.sync(ws) == eb.ERR_TIMEOUT
     plan.run(x, y, 4, ws)
     assert plan.sync(ws) == 0
+
+
+@pytest.mark.parametrize("dims,dtype", [((256, 611), 1), ((261, 401), 2), ((64, 96), 0)])
+def test_tune_asks_for_more_candidates_than_ranked(dims, dtype):
+    """Small grids give the cost model few shared-memory candidates; asking
+    the tuner for more must time only real ones and leave a runnable plan."""
+    eb = _eb()
+    g, c = synth.problem(2, dims, 1, 1, synth.DIRICHLET, seed=17)
+    x = torch.from_numpy(g).to(eb.torch_dtype(dtype)).cuda()
+    plan = eb.Plan(2, dims, 1, 1, c, dtype, eb.DIRICHLET)
+    ws = plan.workspace()
+    y = torch.empty_like(x)
+    plan.tune(x, y, 16, ws, max_candidates=64)
+    plan.run(x, y, 9, ws)
+    yn = torch.empty_like(x)
+    plan.run(x, yn, 9, ws, naive=True)
+    assert plan.sync(ws) == 0
+    assert torch.equal(y, yn)
