@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-STAR, BOX = 0, 1
+STAR, BOX, POISSON, J3D17 = 0, 1, 2, 3
 DIRICHLET, PERIODIC = 0, 1
 
 _lib = None
@@ -56,6 +56,11 @@ def _load():
         lib.oracle_run.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                    ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_run_offsets.restype = ctypes.c_int
+        lib.oracle_run_offsets.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
+                                           ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
         lib.oracle_reduce.restype = ctypes.c_int
         lib.oracle_reduce.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
@@ -98,6 +103,29 @@ def run(grid: np.ndarray, shape: int, radius: int, coeffs, boundary: int,
                         g.ctypes.data, out.ctypes.data, int(steps), int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle_run failed ({rc})")
+    return out
+
+
+def run_offsets(grid: np.ndarray, offsets, radius: int, coeffs, boundary: int, steps: int,
+                nthreads: int = 0) -> np.ndarray:
+    """`steps` Jacobi steps with an explicit offset list: `offsets` is a
+    sequence of (dz, dy, dx) triples (dz = 0 in 2D), summed in the order
+    given; `radius` is the pad width (Dirichlet) and bounds every offset."""
+    lib = _load()
+    g = np.ascontiguousarray(grid, dtype=np.float64)
+    o = np.ascontiguousarray(np.asarray(offsets, dtype=np.int32).reshape(-1, 3))
+    c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    if c.size != o.shape[0]:
+        raise ValueError("one coefficient per offset")
+    pad = radius if boundary == DIRICHLET else 0
+    dims = (ctypes.c_int64 * g.ndim)(*[s - 2 * pad for s in g.shape])
+    oz, oy, ox = (np.ascontiguousarray(o[:, i]) for i in range(3))
+    out = np.empty_like(g)
+    rc = lib.oracle_run_offsets(g.ndim, dims, radius, int(o.shape[0]), oz.ctypes.data, oy.ctypes.data,
+                                ox.ctypes.data, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), boundary,
+                                g.ctypes.data, out.ctypes.data, int(steps), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_run_offsets failed ({rc})")
     return out
 
 

@@ -22,6 +22,16 @@
  *   - Canonical offsets: the support set sorted lexicographically by
  *     (dz, dy, dx).  Star = the centre plus the axis offsets with |k| <= r;
  *     box = every offset with max|k| <= r.
+ *   - Table 2 lists two more 3D order-1 stencils without their offsets:
+ *     poisson [order 1, 38 flops: 19 points] and j3d17pt [order 1, 34 flops:
+ *     17 points], both within the 27-point box (the paper runs its
+ *     comparison systems' 27-point code for them).  Poisson = the box without
+ *     its 8 corners (offsets with at most two nonzero components).  No
+ *     17-point subset of the box has the cube's full symmetry; the reading
+ *     here is the poisson set without the two z-axis neighbours (0,0,+-1):
+ *     the full 3x3 box in the z = 0 plane plus the four in-plane axis
+ *     neighbours (dy,dx) = (+-1,0), (0,+-1) in each of the planes z = +-1.
+ *   - Any other offset set runs through oracle_run_offsets.
  *   - Dirichlet: the array is padded by r cells on every side; the pad holds
  *     its initial values for every step (it is read, never written).
  *   - Periodic: the array is not padded; neighbour indices wrap modulo n.
@@ -39,6 +49,8 @@
 
 #define OR_STAR 0
 #define OR_BOX 1
+#define OR_POISSON 2
+#define OR_J3D17 3
 #define OR_DIRICHLET 0
 #define OR_PERIODIC 1
 
@@ -46,7 +58,9 @@
  * dz/dy/dx (each may be NULL to only count) and returns npts, or -1. */
 int oracle_offsets(int ndim, int shape, int radius, int* dz, int* dy, int* dx)
 {
-    if ((ndim != 2 && ndim != 3) || radius < 1 || (shape != OR_STAR && shape != OR_BOX))
+    if ((ndim != 2 && ndim != 3) || radius < 1 || shape < OR_STAR || shape > OR_J3D17)
+        return -1;
+    if ((shape == OR_POISSON || shape == OR_J3D17) && (ndim != 3 || radius != 1))
         return -1;
     int zr = (ndim == 3) ? radius : 0;
     int n = 0;
@@ -55,6 +69,10 @@ int oracle_offsets(int ndim, int shape, int radius, int* dz, int* dy, int* dx)
             for (int c = -radius; c <= radius; c++) {
                 int nonzero = (a != 0) + (b != 0) + (c != 0);
                 if (shape == OR_STAR && nonzero > 1)
+                    continue;
+                if ((shape == OR_POISSON || shape == OR_J3D17) && nonzero > 2)
+                    continue;
+                if (shape == OR_J3D17 && a != 0 && b == 0 && c == 0)
                     continue;
                 if (dz) dz[n] = a;
                 if (dy) dy[n] = b;
@@ -111,21 +129,28 @@ static void one_step(const int64_t ext[3], const int64_t n[3], int pad,
     }
 }
 
-/* Run `steps` Jacobi steps.
+/* Run `steps` Jacobi steps of the stencil with the given offsets.
  *   dims: interior extents, slowest first ((ny, nx) or (nz, ny, nx)).
- *   coeffs: npts values in canonical order.
+ *   radius: pad width of a Dirichlet grid; every |offset component| must be
+ *   <= radius (2D: dz = 0).
+ *   oz/oy/ox/coeffs: npts offsets and their weights, summed in the order
+ *   given (callers pass the canonical order).
  *   in/out: stored arrays (padded by `radius` for Dirichlet); `in` is not
  *   modified; out may not alias in.  steps == 0 copies in to out.
  *   nthreads <= 0 means "all available". */
-int oracle_run(int ndim, const int64_t* dims, int shape, int radius,
-               const double* coeffs, int boundary, const double* in,
-               double* out, int64_t steps, int nthreads)
+int oracle_run_offsets(int ndim, const int64_t* dims, int radius, int npts, const int* oz,
+                       const int* oy, const int* ox, const double* coeffs, int boundary,
+                       const double* in, double* out, int64_t steps, int nthreads)
 {
-    int npts = oracle_offsets(ndim, shape, radius, NULL, NULL, NULL);
-    if (npts < 0 || steps < 0 || !dims || !coeffs || !in || !out || in == out)
+    if ((ndim != 2 && ndim != 3) || radius < 1 || npts < 1 || steps < 0 || !dims || !coeffs || !in ||
+        !out || in == out || !oz || !oy || !ox)
         return -1;
     if (boundary != OR_DIRICHLET && boundary != OR_PERIODIC)
         return -1;
+    for (int k = 0; k < npts; k++) {
+        if (abs(oz[k]) > radius || abs(oy[k]) > radius || abs(ox[k]) > radius) return -1;
+        if (ndim == 2 && oz[k] != 0) return -1;
+    }
     int64_t n[3] = {1, 1, 1};
     for (int d = 0; d < ndim; d++) {
         if (dims[d] < 1) return -1;
@@ -137,15 +162,8 @@ int oracle_run(int ndim, const int64_t* dims, int shape, int radius,
         ext[d] = n[d] + ((d >= 3 - ndim) ? 2 * pad : 0);
     int64_t total = ext[0] * ext[1] * ext[2];
 
-    int* oz = malloc(sizeof(int) * npts);
-    int* oy = malloc(sizeof(int) * npts);
-    int* ox = malloc(sizeof(int) * npts);
     double* tmp = malloc(sizeof(double) * (size_t)total);
-    if (!oz || !oy || !ox || !tmp) {
-        free(oz); free(oy); free(ox); free(tmp);
-        return -2;
-    }
-    oracle_offsets(ndim, shape, radius, oz, oy, ox);
+    if (!tmp) return -2;
 #ifdef _OPENMP
     if (nthreads <= 0) nthreads = omp_get_max_threads();
 #else
@@ -163,8 +181,32 @@ int oracle_run(int ndim, const int64_t* dims, int shape, int radius,
                  coeffs, a, b, nthreads);
         double* t = a; a = b; b = t;
     }
-    free(oz); free(oy); free(ox); free(tmp);
+    free(tmp);
     return 0;
+}
+
+/* Run `steps` Jacobi steps of a named stencil (star, box, poisson, j3d17pt;
+ * offsets from oracle_offsets, canonical order).  Arguments as for
+ * oracle_run_offsets. */
+int oracle_run(int ndim, const int64_t* dims, int shape, int radius,
+               const double* coeffs, int boundary, const double* in,
+               double* out, int64_t steps, int nthreads)
+{
+    int npts = oracle_offsets(ndim, shape, radius, NULL, NULL, NULL);
+    if (npts < 0)
+        return -1;
+    int* oz = malloc(sizeof(int) * npts);
+    int* oy = malloc(sizeof(int) * npts);
+    int* ox = malloc(sizeof(int) * npts);
+    if (!oz || !oy || !ox) {
+        free(oz); free(oy); free(ox);
+        return -2;
+    }
+    oracle_offsets(ndim, shape, radius, oz, oy, ox);
+    int rc = oracle_run_offsets(ndim, dims, radius, npts, oz, oy, ox, coeffs, boundary, in, out, steps,
+                                nthreads);
+    free(oz); free(oy); free(ox);
+    return rc;
 }
 
 /* Interior reductions used for verification and reporting (FP64):

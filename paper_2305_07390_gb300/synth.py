@@ -20,7 +20,7 @@ import numpy as np
 
 DEFAULT_SEED = 20230521
 
-STAR, BOX = 0, 1
+STAR, BOX, POISSON, J3D17 = 0, 1, 2, 3
 DIRICHLET, PERIODIC = 0, 1
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -55,6 +55,10 @@ def npoints(ndim: int, shape: int, radius: int) -> int:
     """Number of support points (a count only; offsets are not built here)."""
     if shape == STAR:
         return 2 * ndim * radius + 1
+    if shape == POISSON:
+        return 19
+    if shape == J3D17:
+        return 17
     return (2 * radius + 1) ** ndim
 
 

@@ -28,11 +28,16 @@ from paper_2305_07390_gb300 import synth
 EPS = np.finfo(np.float64).eps
 
 SHAPES_2D = [(synth.STAR, 1), (synth.STAR, 2), (synth.STAR, 3), (synth.BOX, 1), (synth.BOX, 2)]
-SHAPES_3D = [(synth.STAR, 1), (synth.STAR, 2), (synth.STAR, 3), (synth.BOX, 1), (synth.BOX, 2)]
+SHAPES_3D = [(synth.STAR, 1), (synth.STAR, 2), (synth.STAR, 3), (synth.BOX, 1), (synth.BOX, 2),
+             (synth.POISSON, 1), (synth.J3D17, 1)]
 
 
 def independent_offsets(ndim, shape, r):
-    """Offset set built from its definition, sorted as (dz, dy, dx) tuples."""
+    """Offset set built from its definition, sorted as (dz, dy, dx) tuples.
+    Poisson: the 27-point box without its corners (Table 2: 19 points, 38
+    flops); j3d17pt (17 points, 34 flops): the reading of that set -- the
+    3x3 box of the z = 0 plane plus the 4 axis neighbours in each of the
+    planes z = -1 and z = +1."""
     rng = range(-r, r + 1)
     if ndim == 2:
         pts = [(0, a, b) for a, b in itertools.product(rng, rng)]
@@ -40,6 +45,10 @@ def independent_offsets(ndim, shape, r):
         pts = list(itertools.product(rng, rng, rng))
     if shape == synth.STAR:
         pts = [p for p in pts if sum(1 for v in p if v != 0) <= 1]
+    if shape == synth.POISSON:
+        pts = [p for p in pts if not all(v != 0 for v in p)]
+    if shape == synth.J3D17:
+        pts = [p for p in pts if p[0] == 0 or (p[1] != 0) != (p[2] != 0)]
     return sorted(pts)
 
 
@@ -50,10 +59,12 @@ def independent_offsets(ndim, shape, r):
 @pytest.mark.parametrize("ndim,shape,r,npts", [
     (2, synth.STAR, 1, 5), (2, synth.STAR, 2, 9), (2, synth.STAR, 3, 13),
     (2, synth.BOX, 1, 9), (2, synth.BOX, 2, 25),
-    (3, synth.STAR, 1, 7), (3, synth.STAR, 2, 13), (3, synth.BOX, 1, 27), (3, synth.BOX, 2, 125)])
+    (3, synth.STAR, 1, 7), (3, synth.STAR, 2, 13), (3, synth.BOX, 1, 27), (3, synth.BOX, 2, 125),
+    (3, synth.POISSON, 1, 19), (3, synth.J3D17, 1, 17)])
 def test_offset_counts_match_table3(ndim, shape, r, npts):
     # Table 2 (benchmarks): j2d5pt, j2d9pt, 2D r3 star, j2d9pt-gol, j2d25pt,
-    # j3d7pt, j3d13pt, j3d27pt and the 125-point box.
+    # j3d7pt, j3d13pt, j3d27pt, the 125-point box, poisson (order 1, 38
+    # flops per cell = 19 points) and j3d17pt (order 1, 34 flops = 17).
     offs = oracle.offsets(ndim, shape, r)
     assert offs.shape == (npts, 3)
     assert [tuple(o) for o in offs] == independent_offsets(ndim, shape, r)
@@ -93,6 +104,62 @@ def test_listing3_3d7pt_expansion():
                     + d * g[s, :-2, s] + e * g[s, 2:, s]
                     + f * g[s, s, :-2] + h * g[s, s, 2:])
     np.testing.assert_allclose(out, ref, rtol=8 * EPS, atol=8 * EPS)
+
+
+def test_new_sets_symmetry_and_flops():
+    # 2 flops per point: Table 2's 38 (poisson) and 34 (j3d17pt)
+    assert 2 * oracle.npoints(3, synth.POISSON, 1) == 38
+    assert 2 * oracle.npoints(3, synth.J3D17, 1) == 34
+    for shape in (synth.POISSON, synth.J3D17):
+        pts = {tuple(o) for o in oracle.offsets(3, shape, 1)}
+        assert all(max(abs(v) for v in p) <= 1 for p in pts)          # order 1
+        assert {tuple(-v for v in p) for p in pts} == pts              # point symmetric
+        assert {(p[0], p[2], p[1]) for p in pts} == pts                # y <-> x
+    pois = {tuple(o) for o in oracle.offsets(3, synth.POISSON, 1)}
+    perms = itertools.permutations(range(3))
+    assert all({tuple(p[i] for i in pm) for p in pois} == pois for pm in perms)  # every axis alike
+    j17 = {tuple(o) for o in oracle.offsets(3, synth.J3D17, 1)}
+    assert j17 == pois - {(-1, 0, 0), (1, 0, 0)}
+
+
+def test_poisson_with_star_weights_is_the_7_point_star():
+    g, c7 = synth.problem(3, (7, 6, 8), synth.STAR, 1, synth.DIRICHLET, seed=14)
+    offs = [tuple(o) for o in oracle.offsets(3, synth.POISSON, 1)]
+    star = [tuple(o) for o in oracle.offsets(3, synth.STAR, 1)]
+    c19 = [c7[star.index(o)] if o in star else 0.0 for o in offs]
+    np.testing.assert_array_equal(oracle.run(g, synth.POISSON, 1, c19, synth.DIRICHLET, 4),
+                                  oracle.run(g, synth.STAR, 1, c7, synth.DIRICHLET, 4))
+
+
+def test_j3d17_with_in_plane_weights_is_a_2d_box_per_plane():
+    rng = np.random.default_rng(15)
+    g = rng.random((6, 9, 10))
+    offs = [tuple(o) for o in oracle.offsets(3, synth.J3D17, 1)]
+    box = [(0, a, b) for a in (-1, 0, 1) for b in (-1, 0, 1)]
+    w = rng.random(9)
+    c17 = [w[box.index(o)] if o in box else 0.0 for o in offs]
+    out = oracle.run(g, synth.J3D17, 1, c17, synth.DIRICHLET, 3)
+    for z in range(1, 5):
+        np.testing.assert_allclose(out[z], oracle.run(g[z], synth.BOX, 1, w, synth.DIRICHLET, 3),
+                                   rtol=1e-15, atol=1e-15)
+
+
+@pytest.mark.parametrize("boundary", [synth.DIRICHLET, synth.PERIODIC])
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_offset_list_bruteforce(ndim, boundary):
+    # an arbitrary, asymmetric offset list inside the radius-2 box
+    rng = np.random.default_rng(16 + ndim)
+    full = independent_offsets(ndim, synth.BOX, 2)
+    pick = sorted(full[i] for i in rng.choice(len(full), 11, replace=False))
+    c = rng.random(11)
+    c /= c.sum()
+    dims = (9, 8) if ndim == 2 else (5, 5, 6)
+    g = synth.grid(dims, 2, boundary, seed=17)
+    M = dense_operator(g.shape, pick, c, 2, boundary)
+    for T in (1, 3):
+        out = oracle.run_offsets(g, pick, 2, c, boundary, T)
+        ref = (np.linalg.matrix_power(M, T) @ g.ravel()).reshape(g.shape)
+        np.testing.assert_allclose(out, ref, rtol=1e-14, atol=1e-14)
 
 
 def test_listing1_1d_special_case():
