@@ -65,7 +65,13 @@ enum ebisu_status {
     EBISU_ERR_BUSY = 9          /* serving: queue full, request rejected      */
 };
 
-enum ebisu_shape { EBISU_STAR = 0, EBISU_BOX = 1 };
+/* Shapes (Table 2): star = centre + axis offsets |k| <= r; box = every
+ * offset with max|k| <= r; and two 3D order-1 sets the paper gives only by
+ * point count -- poisson (19 points: the 27-point box without its corners)
+ * and j3d17pt (17 points; the library's reading: poisson without the two
+ * z-axis neighbours, i.e. the z = 0 plane's 3x3 box plus the four in-plane
+ * axis neighbours (dy,dx) = (+-1,0), (0,+-1) in each plane z = +-1). */
+enum ebisu_shape { EBISU_STAR = 0, EBISU_BOX = 1, EBISU_POISSON = 2, EBISU_J3D17PT = 3 };
 enum ebisu_dtype { EBISU_F64 = 0, EBISU_F32 = 1, EBISU_BF16 = 2 };
 enum ebisu_boundary { EBISU_DIRICHLET = 0, EBISU_PERIODIC = 1 };
 enum ebisu_rounding { EBISU_ROUND_NEAREST = 0, EBISU_ROUND_STOCHASTIC = 1 };
@@ -123,11 +129,12 @@ int ebisu_version(void);
  *   ndim      : 2 or 3.
  *   dims      : host array of ndim interior extents, slowest first, each >= 1
  *               (periodic: each >= 2*radius+1).
- *   shape     : EBISU_STAR (centre + axis offsets |k| <= r) or EBISU_BOX
- *               (all offsets with max |k| <= r); Table 2 of the paper.
- *   radius    : 1..3 for star, 1..2 for box.
+ *   shape     : enum ebisu_shape (Table 2 of the paper).
+ *   radius    : 1..3 for star, 1..2 for box, 1 for poisson and j3d17pt
+ *               (3D only).
  *   coeffs    : host array of P weights in canonical offset order
- *               (P = 2*ndim*r+1 for star, (2r+1)^ndim for box); copied.
+ *               (P = 2*ndim*r+1 for star, (2r+1)^ndim for box, 19 for
+ *               poisson, 17 for j3d17pt); copied.
  *   dtype     : storage type (enum ebisu_dtype).
  *   boundary  : EBISU_DIRICHLET (padded, fixed pad) or EBISU_PERIODIC.
  *   out       : receives the plan.
@@ -136,6 +143,21 @@ int ebisu_version(void);
 int ebisu_plan_create(int ndim, const int64_t* dims, int shape, int radius,
                       const double* coeffs, int dtype, int boundary,
                       ebisu_plan_t* out);
+
+/* Create a plan from an explicit offset list (any support set; Section
+ * 2.1's update with the given offsets).
+ *   offsets : host array of npts (dz, dy, dx) triples (2D: dz = 0), no
+ *             repeats; the radius is the largest |component| (1..3).
+ *   coeffs  : npts weights, one per offset (any order: the sum is taken in
+ *             canonical order, as for the named shapes).
+ * A list whose set is exactly a named shape's gets that shape's kernels.
+ * Any other list runs on the box of its radius (radius <= 2) with zero
+ * weights on the offsets it lacks: for finite values the sum is the same,
+ * at the box's arithmetic cost.  A non-star list of radius 3 returns
+ * EBISU_ERR_UNSUPPORTED.  Otherwise as ebisu_plan_create. */
+int ebisu_plan_create_offsets(int ndim, const int64_t* dims, int npts,
+                              const int32_t* offsets, const double* coeffs,
+                              int dtype, int boundary, ebisu_plan_t* out);
 
 /* Destroy a plan.  Plans may be destroyed while work that used them is still
  * in flight: launches copy what they need. */

@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(kRedThreads) reduce_partial_kernel(const T* __
 
 #define EBISU_FOR_EACH_STENCIL(X) \
     X(2, kStar, 1) X(2, kStar, 2) X(2, kStar, 3) X(2, kBox, 1) X(2, kBox, 2) \
-    X(3, kStar, 1) X(3, kStar, 2) X(3, kStar, 3) X(3, kBox, 1) X(3, kBox, 2)
+    X(3, kStar, 1) X(3, kStar, 2) X(3, kStar, 3) X(3, kBox, 1) X(3, kBox, 2) \
+    X(3, kPoisson, 1) X(3, kJ3d17, 1)
 
 constexpr int kTBThreads = 256;
 constexpr int kTBStage = 16;

@@ -3,6 +3,7 @@
 #include "stencil.cuh"  // the stochastic-rounding keys (host side)
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -537,11 +538,13 @@ int ebisu_plan_create(int ndim, const int64_t* dims, int shape, int radius, cons
     if (!out || !dims || !coeffs) return EBISU_ERR_INVALID_ARG;
     *out = nullptr;
     if (ndim != 2 && ndim != 3) return EBISU_ERR_INVALID_ARG;
-    if (shape != EBISU_STAR && shape != EBISU_BOX) return EBISU_ERR_INVALID_ARG;
+    if (shape < EBISU_STAR || shape > EBISU_J3D17PT) return EBISU_ERR_INVALID_ARG;
     if (dtype != EBISU_F64 && dtype != EBISU_F32 && dtype != EBISU_BF16) return EBISU_ERR_INVALID_ARG;
     if (boundary != EBISU_DIRICHLET && boundary != EBISU_PERIODIC) return EBISU_ERR_INVALID_ARG;
     if (radius < 1) return EBISU_ERR_INVALID_ARG;
     if ((shape == EBISU_STAR && radius > 3) || (shape == EBISU_BOX && radius > 2)) return EBISU_ERR_UNSUPPORTED;
+    if ((shape == EBISU_POISSON || shape == EBISU_J3D17PT) && (ndim != 3 || radius != 1))
+        return EBISU_ERR_UNSUPPORTED;
     for (int i = 0; i < ndim; ++i) {
         if (dims[i] < 1) return EBISU_ERR_INVALID_ARG;
         if (boundary == EBISU_PERIODIC && dims[i] < 2 * radius + 1) return EBISU_ERR_UNSUPPORTED;
@@ -555,9 +558,10 @@ int ebisu_plan_create(int ndim, const int64_t* dims, int shape, int radius, cons
     p->dtype = dtype;
     p->boundary = boundary;
     for (int i = 0; i < ndim; ++i) p->dims[i] = dims[i];
-    p->npts = (shape == EBISU_STAR) ? 2 * ndim * radius + 1
-                                    : (ndim == 3 ? (2 * radius + 1) * (2 * radius + 1) * (2 * radius + 1)
-                                                 : (2 * radius + 1) * (2 * radius + 1));
+    p->npts = (shape == EBISU_STAR)      ? 2 * ndim * radius + 1
+              : (shape == EBISU_POISSON) ? 19
+              : (shape == EBISU_J3D17PT) ? 17
+              : (ndim == 3 ? (2 * radius + 1) * (2 * radius + 1) * (2 * radius + 1) : (2 * radius + 1) * (2 * radius + 1));
     for (int k = 0; k < p->npts; ++k) p->coef[k] = coeffs[k];
     p->esize = (dtype == EBISU_F64) ? 8 : (dtype == EBISU_F32 ? 4 : 2);
     p->pad = (boundary == EBISU_DIRICHLET) ? radius : 0;
@@ -615,6 +619,76 @@ int ebisu_plan_create(int ndim, const int64_t* dims, int shape, int radius, cons
     }
     *out = p;
     return EBISU_OK;
+}
+
+// Offsets of a named shape in canonical order (the kernels' tables, host side).
+static int shape_offsets(int ndim, int shape, int r, int* oz, int* oy, int* ox)
+{
+    int n = 0;
+    const int zr = ndim == 3 ? r : 0;
+    for (int a = -zr; a <= zr; ++a)
+        for (int b = -r; b <= r; ++b)
+            for (int c = -r; c <= r; ++c) {
+                const int nz = (a != 0) + (b != 0) + (c != 0);
+                if (shape == EBISU_STAR && nz > 1) continue;
+                if ((shape == EBISU_POISSON || shape == EBISU_J3D17PT) && nz > 2) continue;
+                if (shape == EBISU_J3D17PT && a != 0 && b == 0 && c == 0) continue;
+                oz[n] = a;
+                oy[n] = b;
+                ox[n] = c;
+                ++n;
+            }
+    return n;
+}
+
+int ebisu_plan_create_offsets(int ndim, const int64_t* dims, int npts, const int32_t* offsets, const double* coeffs,
+                              int dtype, int boundary, ebisu_plan_t* out)
+{
+    if (!out || !dims || !offsets || !coeffs || npts < 1 || npts > kMaxPoints) return EBISU_ERR_INVALID_ARG;
+    if (ndim != 2 && ndim != 3) return EBISU_ERR_INVALID_ARG;
+    *out = nullptr;
+    int r = 0;
+    for (int k = 0; k < npts; ++k) {
+        const int32_t* o = offsets + 3 * k;
+        if (ndim == 2 && o[0] != 0) return EBISU_ERR_INVALID_ARG;
+        for (int i = 0; i < 3; ++i) r = std::max(r, std::abs(o[i]));
+        for (int j = 0; j < k; ++j)
+            if (o[0] == offsets[3 * j] && o[1] == offsets[3 * j + 1] && o[2] == offsets[3 * j + 2])
+                return EBISU_ERR_INVALID_ARG;  // repeated offset
+    }
+    if (r < 1) r = 1;
+    if (r > 3) return EBISU_ERR_UNSUPPORTED;
+    // the coefficient of offset (a, b, c), 0 where the list has none
+    auto coef_of = [&](int a, int b, int c, bool* found) {
+        for (int k = 0; k < npts; ++k)
+            if (offsets[3 * k] == a && offsets[3 * k + 1] == b && offsets[3 * k + 2] == c) {
+                *found = true;
+                return coeffs[k];
+            }
+        *found = false;
+        return 0.0;
+    };
+    // a named shape whose set is exactly the list runs its own kernels;
+    // any other list runs on the box of its radius with zero weights on the
+    // offsets it lacks (x + 0*u = x for finite u, so the sum is unchanged)
+    int oz[kMaxPoints], oy[kMaxPoints], ox[kMaxPoints];
+    double c[kMaxPoints];
+    for (int shape : {EBISU_STAR, EBISU_POISSON, EBISU_J3D17PT, EBISU_BOX}) {
+        if ((shape == EBISU_POISSON || shape == EBISU_J3D17PT) && (ndim != 3 || r != 1)) continue;
+        if (shape == EBISU_BOX && r > 2) continue;
+        const int n = shape_offsets(ndim, shape, r, oz, oy, ox);
+        bool covers = true;
+        int matched = 0;
+        for (int k = 0; k < n; ++k) {
+            bool f = false;
+            c[k] = coef_of(oz[k], oy[k], ox[k], &f);
+            matched += f ? 1 : 0;
+        }
+        if (matched != npts) covers = false;  // some offset lies outside this shape
+        if (!covers || (shape != EBISU_BOX && n != npts)) continue;
+        return ebisu_plan_create(ndim, dims, shape, r, c, dtype, boundary, out);
+    }
+    return EBISU_ERR_UNSUPPORTED;  // radius 3 and not a star: no box of that radius is built
 }
 
 int ebisu_plan_destroy(ebisu_plan_t plan)

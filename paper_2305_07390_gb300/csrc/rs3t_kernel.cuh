@@ -56,7 +56,7 @@ struct RS3TGeom {
         return o;
     }
     static constexpr int RING = off(D);  // levels 0 .. D-1
-    static constexpr int regs() { return RING + rows(1) * VX + (SHAPE == kBox ? 18 : 0) + 80; }
+    static constexpr int regs() { return RING + rows(1) * VX + (SHAPE != kStar ? 18 : 0) + 80; }
     static constexpr int minb()
     {
         const int e = (regs() + 7) & ~7;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
 #pragma unroll
                     for (int i = 0; i < G::rows(s); ++i) {
                         const int ib = i + 1;  // the same row in level s-1
-                        if constexpr (SHAPE == kBox) {
+                        if constexpr (SHAPE != kStar) {
                             // rows ib-1 .. ib+1 of all three planes; the first
                             // two were shuffled for earlier rows
                             if (i == 0) {

@@ -66,10 +66,15 @@ static const void* rs_ptr_pick(int depth)
             if (shape == kStar && r == 1) return (const void*)&rs3_kernel<T, kStar, 1>;                \
             if (shape == kStar && r == 2) return (const void*)&rs3_kernel<T, kStar, 2>;                \
             if (shape == kBox && r == 1) return (const void*)&rs3_kernel<T, kBox, 1>;                  \
+            if (shape == kPoisson && r == 1) return (const void*)&rs3_kernel<T, kPoisson, 1>;          \
+            if (shape == kJ3d17 && r == 1) return (const void*)&rs3_kernel<T, kJ3d17, 1>;              \
         } else {                                                                                       \
             if (r == 1 && shape == kStar && depth == 2) return (const void*)&rs3t_kernel<T, kStar, 2>; \
             if (r == 1 && shape == kStar && depth == 3) return (const void*)&rs3t_kernel<T, kStar, 3>; \
             if (r == 1 && shape == kBox && depth == 2) return (const void*)&rs3t_kernel<T, kBox, 2>;   \
+            if (r == 1 && shape == kPoisson && depth == 2)                                             \
+                return (const void*)&rs3t_kernel<T, kPoisson, 2>;                                      \
+            if (r == 1 && shape == kJ3d17 && depth == 2) return (const void*)&rs3t_kernel<T, kJ3d17, 2>; \
         }                                                                                              \
         (void)shape; (void)r; (void)depth;                                                             \
         return nullptr;                                                                                \

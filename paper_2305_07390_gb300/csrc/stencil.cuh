@@ -14,7 +14,13 @@
 
 namespace ebisu {
 
-enum { kStar = 0, kBox = 1 };
+// Shapes: star (centre + axis offsets |k| <= r), box (every offset with
+// max |k| <= r), and two 3D order-1 sets of Table 2: poisson (the 27-point
+// box without its corners, 19 points) and j3d17pt (17 points: poisson
+// without the z-axis neighbours -- the z = 0 plane's 3x3 box plus the four
+// in-plane axis neighbours in each of the planes z = +-1; the paper lists
+// only the point count, this is the library's reading).
+enum { kStar = 0, kBox = 1, kPoisson = 2, kJ3d17 = 3 };
 
 // ---------------------------------------------------------------------------
 // Canonical offsets, expressed in streaming coordinates: `s` is the slowest
@@ -26,9 +32,26 @@ struct Stencil {
     static constexpr int kR = R;
     static constexpr int kDim = DIM;
     static constexpr int kRP1 = (DIM == 3) ? R : 0;  // radius along p1
-    static constexpr int P = (SHAPE == kStar) ? (2 * DIM * R + 1)
-                                              : ((DIM == 3) ? (2 * R + 1) * (2 * R + 1) * (2 * R + 1)
-                                                            : (2 * R + 1) * (2 * R + 1));
+    static_assert(SHAPE == kStar || SHAPE == kBox || (DIM == 3 && R == 1), "poisson and j3d17pt: 3D, radius 1");
+    // is (a, b, c) = (ds, d1, d2) in the support set?
+    static constexpr bool member(int a, int b, int c)
+    {
+        const int nz = (a != 0) + (b != 0) + (c != 0);
+        if (SHAPE == kStar) return nz <= 1;
+        if (SHAPE == kPoisson) return nz <= 2;
+        if (SHAPE == kJ3d17) return nz <= 2 && !(a != 0 && b == 0 && c == 0);
+        return true;
+    }
+    static constexpr int count()
+    {
+        int n = 0;
+        const int zr = (DIM == 3) ? R : 0;
+        for (int a = -zr; a <= zr; ++a)
+            for (int b = -R; b <= R; ++b)
+                for (int c = -R; c <= R; ++c) n += member(DIM == 3 ? a : 0, b, c) ? 1 : 0;
+        return n;
+    }
+    static constexpr int P = count();
     struct Table {
         int ds[P];
         int d1[P];
@@ -42,8 +65,7 @@ struct Stencil {
         for (int a = -zr; a <= zr; ++a)
             for (int b = -R; b <= R; ++b)
                 for (int c = -R; c <= R; ++c) {
-                    const int nz = (a != 0) + (b != 0) + (c != 0);
-                    if (SHAPE == kStar && nz > 1) continue;
+                    if (!member(a, b, c)) continue;
                     if (DIM == 3) {
                         t.ds[n] = a; t.d1[n] = b; t.d2[n] = c;
                     } else {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libebisu.so")
 
 (OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_OOM, ERR_BUDGET, ERR_TIMEOUT, ERR_DEVICE_FAULT,
  ERR_NOT_READY, ERR_BUSY) = range(10)
-STAR, BOX = 0, 1
+STAR, BOX, POISSON, J3D17PT = 0, 1, 2, 3
 F64, F32, BF16 = 0, 1, 2
 DIRICHLET, PERIODIC = 0, 1
 ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1
@@ -73,6 +73,8 @@ SIGNATURES = {
     "ebisu_version": (_I, []),
     "ebisu_last_cuda_error": (ctypes.c_char_p, []),
     "ebisu_plan_create": (_I, [_I, ctypes.POINTER(_I64), _I, _I, ctypes.POINTER(_D), _I, _I, ctypes.POINTER(_P)]),
+    "ebisu_plan_create_offsets": (_I, [_I, ctypes.POINTER(_I64), _I, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(_D), _I, _I, ctypes.POINTER(_P)]),
     "ebisu_plan_destroy": (_I, [_P]),
     "ebisu_plan_npoints": (_I, [_P, ctypes.POINTER(_I)]),
     "ebisu_plan_grid_elems": (_I, [_P, ctypes.POINTER(_I64)]),
@@ -220,14 +222,34 @@ def current_stream_handle():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def ebisu_plan_create_offsets(ndim, dims, offsets, coeffs, dtype, boundary):
+    h = _P()
+    flat = [int(v) for o in offsets for v in o]
+    d = (_I64 * ndim)(*[int(x) for x in dims])
+    o = (ctypes.c_int32 * len(flat))(*flat)
+    c = (_D * len(coeffs))(*[float(x) for x in coeffs])
+    _check(lib().ebisu_plan_create_offsets(ndim, d, len(coeffs), o, c, dtype, boundary, ctypes.byref(h)),
+           "ebisu_plan_create_offsets")
+    return h
+
+
 class Plan:
     """Owns a plan handle; runs on torch CUDA tensors laid out as the C ABI says."""
 
-    def __init__(self, ndim, dims, shape, radius, coeffs, dtype=F64, boundary=DIRICHLET):
+    def __init__(self, ndim, dims, shape, radius, coeffs, dtype=F64, boundary=DIRICHLET, offsets=None):
         self.ndim, self.dims, self.shape, self.radius = ndim, tuple(int(d) for d in dims), shape, radius
         self.dtype, self.boundary = dtype, boundary
         self.coeffs = [float(c) for c in coeffs]
-        self.h = ebisu_plan_create(ndim, dims, shape, radius, coeffs, dtype, boundary)
+        if offsets is None:
+            self.h = ebisu_plan_create(ndim, dims, shape, radius, coeffs, dtype, boundary)
+        else:
+            self.h = ebisu_plan_create_offsets(ndim, dims, offsets, coeffs, dtype, boundary)
+
+    @classmethod
+    def from_offsets(cls, ndim, dims, offsets, coeffs, dtype=F64, boundary=DIRICHLET):
+        """A plan for an explicit offset list ((dz, dy, dx) triples, one weight each)."""
+        r = max(max(abs(v) for v in o) for o in offsets)
+        return cls(ndim, dims, None, max(r, 1), coeffs, dtype, boundary, offsets=offsets)
 
     def __del__(self):
         h = getattr(self, "h", None)

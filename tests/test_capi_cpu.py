@@ -191,3 +191,36 @@ def test_stochastic_rounding_host_rules():
     p.set_rounding(ebisu.ROUND_NEAREST)
     p.set_params(tile_x=64, tile_s=32, depth=2)
     assert p.params().variant == 0
+
+
+def _npts(plan):
+    v = ctypes.c_int()
+    assert ebisu.lib().ebisu_plan_npoints(plan.h, ctypes.byref(v)) == 0
+    return v.value
+
+
+def test_new_shapes_and_offset_lists_host_rules():
+    import itertools
+    p = ebisu.Plan(3, (10, 10, 10), ebisu.POISSON, 1, [1.0 / 19] * 19)
+    assert _npts(p) == 19
+    assert _npts(ebisu.Plan(3, (10, 10, 10), ebisu.J3D17PT, 1, [1.0 / 17] * 17)) == 17
+    for args in [(2, (10, 10), ebisu.POISSON, 1, [0.1] * 19), (3, (10, 10, 10), ebisu.J3D17PT, 2, [0.1] * 17)]:
+        with pytest.raises(ebisu.EbisuError) as ei:
+            ebisu.Plan(*args)
+        assert ei.value.code == ebisu.ERR_UNSUPPORTED
+    # offset lists: a named shape's set gets that shape, others the box of their radius
+    star3 = [(0, 0, k) for k in range(-3, 4)] + [(0, k, 0) for k in range(-3, 4) if k]
+    assert _npts(ebisu.Plan.from_offsets(2, (40, 40), star3, [1.0 / 13] * 13)) == 13
+    odd = [(0, -1, 2), (0, 0, 0), (0, 2, -2)]
+    assert _npts(ebisu.Plan.from_offsets(2, (40, 40), odd, [0.2, 0.5, 0.3])) == 25
+    box1 = list(itertools.product((-1, 0, 1), repeat=3))
+    pois = [o for o in box1 if not all(o)]
+    assert _npts(ebisu.Plan.from_offsets(3, (9, 9, 9), pois[::-1], [1.0 / 19] * 19)) == 19
+    bad = [((0, 0, 0), (0, 0, 0)), ((1, 0, 0), (0, 0, 1))]  # repeated; dz in 2D
+    for offs in bad:
+        with pytest.raises(ebisu.EbisuError) as ei:
+            ebisu.Plan.from_offsets(2, (40, 40), offs, [0.5, 0.5])
+        assert ei.value.code == ebisu.ERR_INVALID_ARG
+    with pytest.raises(ebisu.EbisuError) as ei:
+        ebisu.Plan.from_offsets(2, (40, 40), [(0, 3, 1), (0, 0, 0)], [0.5, 0.5])  # radius 3, not a star
+    assert ei.value.code == ebisu.ERR_UNSUPPORTED

@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {0: 1e-12, 1: 1e-5, 2: 2e-2}
 STENCILS_2D = [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2)]
-STENCILS_3D = [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2)]
+STENCILS_3D = [(0, 1), (0, 2), (0, 3), (1, 1), (1, 2), (2, 1), (3, 1)]  # + poisson, j3d17pt
 
 
 def _eb():
@@ -222,3 +222,49 @@ def test_config1_small_exact_case():
     assert torch.equal(yb, yn)
     ref = oracle.run(g, 0, 1, c, 0, 8)
     assert rel_err(yb, ref, 1) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("ndim", [2, 3])
+@pytest.mark.parametrize("boundary", [0, 1])
+def test_offset_list_plans(ndim, dtype, boundary):
+    """Plans from explicit offset lists: an asymmetric subset of the
+    radius-2 box runs on the box kernels with zero weights elsewhere; the
+    oracle steps the list itself."""
+    eb = _eb()
+    import itertools
+    rng = np.random.default_rng(50 + ndim)
+    rr = range(-2, 3)
+    full = [(0, a, b) for a, b in itertools.product(rr, rr)] if ndim == 2 else list(itertools.product(rr, rr, rr))
+    pick = [full[i] for i in sorted(rng.choice(len(full), 11, replace=False))]
+    pick = sorted(set(pick) | {(0, 0, 2)})  # radius 2 reached along x
+    c = rng.random(len(pick))
+    c /= c.sum()
+    dims = (90, 150) if ndim == 2 else (24, 30, 40)
+    g = synth.grid(dims, 2, boundary, seed=51)
+    x = torch.from_numpy(g).to(eb.torch_dtype(dtype)).cuda()
+    held = x.double().cpu().numpy()
+    c_held = c if dtype == 0 else c.astype(np.float32).astype(np.float64)
+    order = rng.permutation(len(pick))  # the list's order does not matter
+    plan = eb.Plan.from_offsets(ndim, dims, [pick[i] for i in order], c[order], dtype, boundary)
+    yb, yn = run_both(eb, plan, x, 6)
+    assert torch.equal(yb, yn)
+    ref = oracle.run_offsets(held, pick, 2, c_held, boundary, 6)
+    assert rel_err(yb, ref, 2 if boundary == 0 else 0) <= TOL[dtype]
+
+
+def test_offset_list_matching_a_named_shape_gets_its_kernels():
+    eb = _eb()
+    offs = [tuple(o) for o in oracle.offsets(3, 2, 1)]  # poisson
+    c = np.full(len(offs), 1.0 / len(offs))
+    plan = eb.Plan.from_offsets(3, (20, 22, 70), offs, c)
+    assert plan.rs_depths() == (1, 1)  # the FP64 3D register-streaming build exists for it
+    n = ctypes_npoints(eb, plan)
+    assert n == 19
+
+
+def ctypes_npoints(eb, plan):
+    import ctypes
+    v = ctypes.c_int()
+    assert eb.lib().ebisu_plan_npoints(plan.h, ctypes.byref(v)) == 0
+    return v.value

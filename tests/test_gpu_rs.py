@@ -155,7 +155,7 @@ def test_rs_tuner_may_pick_it():
 
 # ---- 3D register streaming (FP64, depth 1: the 7-point star, the 27-point box)
 
-@pytest.mark.parametrize("shape,r", [(0, 1), (1, 1), (0, 2)])
+@pytest.mark.parametrize("shape,r", [(0, 1), (1, 1), (0, 2), (2, 1), (3, 1)])
 @pytest.mark.parametrize("boundary", [0, 1])
 @pytest.mark.parametrize("tile_s", [0, 7, 16])
 def test_rs3_parity(shape, r, boundary, tile_s):
@@ -223,7 +223,7 @@ def test_rs3_wait_timeout_reports_status(monkeypatch):
 # the 7-point star at depth 2, 3; the 27-point box at depth 2)
 
 @pytest.mark.parametrize("dtype", [1, 2])
-@pytest.mark.parametrize("shape", [0, 1])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
 @pytest.mark.parametrize("boundary", [0, 1])
 @pytest.mark.parametrize("which", [0, 1])
 @pytest.mark.parametrize("steps", [1, 5, 7])
