@@ -429,7 +429,9 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
     rounded to half powers of two): the bucket's first grid is tuned, the
     others take its parameters.  The error of each form is checked against
     the oracle on the sampled grids small enough for it (whole grids), and
-    optionally the same grids are timed one launch each."""
+    optionally the same grids are timed one launch each.  Each bucket is
+    tuned with its share of the GPU inside the batch (its grid's cells over
+    the batch's cells), so the streamed bands stay tall."""
     import numpy as np
     import torch
     from paper_2305_07390_gb300 import ebisu, synth
@@ -468,8 +470,9 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
             y = torch.empty_like(x)
             key = (round(2 * math.log2(ny)), round(2 * math.log2(nx)))
             if key not in tuned:
+                # the grid's share of the GPU inside the batch: its cells over the total
                 ws = plan.workspace()
-                plan.tune(x, y, 32, ws, max_candidates=6)
+                plan.tune(x, y, 32, ws, max_candidates=6, share=min(1.0, ny * nx / cells))
                 tuned[key] = plan.params()
                 del ws
             elif not apply_params(ebisu, plan, tuned[key]):

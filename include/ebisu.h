@@ -299,6 +299,16 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out,
                     int64_t steps, void* workspace, int max_candidates,
                     double* best_ms, void* stream);
 
+/* ebisu_plan_tune for a plan that will share the GPU: `share` (0 < share
+ * <= 1) is the fraction of the GPU's resident warps it can expect, e.g. its
+ * cells over a batch's total cells.  The candidates' streamed bands (tile_s)
+ * are sized to fill that share instead of the whole GPU, so a batch member
+ * keeps tall bands and little overlap; the timing itself runs the plan
+ * alone.  share = 1 is ebisu_plan_tune. */
+int ebisu_plan_tune_share(ebisu_plan_t plan, const void* in, void* out,
+                          int64_t steps, void* workspace, int max_candidates,
+                          double share, double* best_ms, void* stream);
+
 /* Cost model of Section 5 for the plan's current parameters on this
  * device.  All outputs are optional (NULL to skip):
  *   pred_cells_per_s : practical attainable performance PP = P x V.
@@ -432,8 +442,10 @@ int ebisu_serve_set_max_queue(ebisu_server_t s, int max_queue);
  *                is that estimate minus the time it has already waited, so
  *                large requests are delayed, never starved.
  *   max_wait_s : > 0 = admission control on predicted delay: a request is
- *                refused (EBISU_ERR_BUSY) when the estimated work already
- *                queued exceeds max_wait_s seconds; 0 = off (the default). */
+ *                refused (EBISU_ERR_BUSY) when the work already queued,
+ *                estimated as above and scaled by the running mean of
+ *                measured over estimated time of finished launches, exceeds
+ *                max_wait_s seconds; 0 = off (the default). */
 enum ebisu_serve_order { EBISU_SERVE_FIFO = 0, EBISU_SERVE_SHORTEST = 1 };
 int ebisu_serve_set_policy(ebisu_server_t s, int order, double max_wait_s);
 

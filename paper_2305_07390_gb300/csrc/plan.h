@@ -77,7 +77,10 @@ size_t tb_smem_bytes(const ebisu_plan_s* p, const ebisu_params& q);
 // Validate a parameter set against the plan and the device.
 int check_params(const ebisu_plan_s* p, const ebisu_params& q);
 // Cost-model ranking (tune.cpp): writes up to `cap` candidates, best first.
-int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, double* pred, int cap);
+// `share` is the fraction of the GPU the plan will have (1 = alone; a batch
+// member gets less), which sizes the streamed bands.
+int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, double* pred, int cap,
+                    double share = 1.0);
 // Cost model of one parameter set (tune.cpp).
 double model_pp(const ebisu_plan_s* p, const ebisu_params& q, int64_t steps, int* bound, double* valid);
 

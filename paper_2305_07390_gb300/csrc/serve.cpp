@@ -54,6 +54,7 @@ struct Request {
 
 struct Launch {
     std::vector<Request*> reqs;
+    double t_start = 0, est_s = 0;  // when it was enqueued; its requests' estimated work
     int lane = -1;
     void* mem = nullptr;
     size_t bytes = 0;
@@ -88,6 +89,9 @@ struct ebisu_server_s {
     int order = EBISU_SERVE_FIFO;
     double max_wait_s = 0;  // admission control: refuse when the predicted wait exceeds it (0 = off)
     double queued_est = 0;  // estimated work of the queued requests (s)
+    // measured over estimated run time of finished launches (running mean),
+    // applied to the queued work when predicting a new request's wait
+    double est_scale = 1.0;
     int device = 0;
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
@@ -129,6 +133,10 @@ struct ebisu_server_s {
                 st = ebisu_batch_sync(L->batch, lanes[L->lane]);
             }
             const double t = now_s();
+            if (st == EBISU_OK && L->est_s > 1e-4) {
+                const double ratio = std::min(10.0, std::max(0.1, (t - L->t_start) / L->est_s));
+                est_scale = 0.8 * est_scale + 0.2 * ratio;
+            }
             for (Request* r : L->reqs) {
                 r->t_done = t;
                 r->status = st;
@@ -154,6 +162,8 @@ struct ebisu_server_s {
         Launch* L = new Launch();
         L->reqs = grp;
         L->lane = lane;
+        L->t_start = now_s();
+        for (Request* r : grp) L->est_s += r->est_s;
         const int n = (int)grp.size();
         std::vector<ebisu_plan_t> plans(n);
         std::vector<int64_t> steps(n);
@@ -361,7 +371,7 @@ int ebisu_serve_submit(ebisu_server_t s, ebisu_plan_t plan, const void* in_dev, 
     }
     // admission control: the queue's length limit, and (if set) the predicted
     // wait -- the estimated work already queued -- against the wait limit
-    const bool late = s->max_wait_s > 0 && s->queued_est > s->max_wait_s;
+    const bool late = s->max_wait_s > 0 && s->queued_est * s->est_scale > s->max_wait_s;
     if (s->queue.size() >= s->max_queue || s->stop || late) {
         ++s->rejected;
         delete r;

@@ -189,7 +189,7 @@ static void push_unique(std::vector<int>& v, int x)
     if (x >= 1 && std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
 }
 
-int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, double* pred, int cap)
+int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, double* pred, int cap, double share)
 {
     const DeviceInfo& dv = device_info();
     std::vector<std::pair<double, ebisu_params>> cand;
@@ -231,7 +231,7 @@ int rank_candidates(const ebisu_plan_s* p, int64_t steps, ebisu_params* out, dou
                     // one or two waves of resident CTAs
                     const int64_t nt2 = (p->n[2] + tx - 1) / tx;
                     const int64_t nt1 = (p->ndim == 3) ? (p->n[1] + ty - 1) / ty : 1;
-                    const int64_t ctas = (int64_t)dv.sms * cps;
+                    const int64_t ctas = std::max<int64_t>(1, (int64_t)((double)dv.sms * cps * share));
                     for (int waves : {1, 2, 4}) {
                         int64_t nts = std::max<int64_t>(1, (ctas * waves + nt2 * nt1 - 1) / (nt2 * nt1));
                         nts = std::min<int64_t>(nts, p->n[0]);
@@ -310,12 +310,19 @@ int ebisu_plan_model(ebisu_plan_t plan, double* pred, int* bound, double* valid)
 int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps, void* workspace,
                     int max_candidates, double* best_ms, void* stream)
 {
+    return ebisu_plan_tune_share(plan, in, out, steps, workspace, max_candidates, 1.0, best_ms, stream);
+}
+
+int ebisu_plan_tune_share(ebisu_plan_t plan, const void* in, void* out, int64_t steps, void* workspace,
+                          int max_candidates, double share, double* best_ms, void* stream)
+{
     if (!plan || !in || !out || !workspace || steps < 1 || max_candidates < 1) return EBISU_ERR_INVALID_ARG;
+    if (!(share > 0.0 && share <= 1.0)) return EBISU_ERR_INVALID_ARG;
     if (in == out) return EBISU_ERR_INVALID_ARG;
     std::vector<ebisu_params> cand(max_candidates);
     std::vector<double> pred(max_candidates);
     const bool sr = plan_sr(plan);
-    int n = sr ? 0 : rank_candidates(plan, steps, cand.data(), pred.data(), max_candidates);
+    int n = sr ? 0 : rank_candidates(plan, steps, cand.data(), pred.data(), max_candidates, share);
     if (n < 1 && !sr) return EBISU_ERR_UNSUPPORTED;
     cand.resize(n);  // the ranking may return fewer than max_candidates
     // (stochastic rounding: no shared-memory build; the one-step kernel keeps
@@ -338,7 +345,7 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
         if (rs3_occupancy(plan, D, &occ) != cudaSuccess || occ < 1) {
             cudaGetLastError();
         } else {
-            const int64_t warps = (int64_t)occ * dv.sms * kRSWarps;
+            const int64_t warps = std::max<int64_t>(1, (int64_t)((double)occ * dv.sms * kRSWarps * share));
             const int64_t S = rs3_strip(es, D, plan->radius), TY = rs3_rows(es);
             const int64_t xy = ((plan->n[2] + S - 1) / S) * ((plan->n[1] + TY - 1) / TY);
             int64_t lastH = -1;
@@ -375,7 +382,7 @@ int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out, int64_t steps,
                 cudaGetLastError();
                 continue;
             }
-            const int64_t warps = (int64_t)occ * dv.sms * kRSWarps;
+            const int64_t warps = std::max<int64_t>(1, (int64_t)((double)occ * dv.sms * kRSWarps * share));
             const int64_t S = kRSCols - 2LL * D * plan->radius;
             const int64_t ns = (plan->n[2] + S - 1) / S;
             int64_t lastH = -1;

@@ -90,6 +90,7 @@ SIGNATURES = {
     "ebisu_sync_static": (_I, [_P]),
     "ebisu_sync": (_I, [_P, _P]),
     "ebisu_plan_tune": (_I, [_P, _P, _P, _I64, _P, _I, ctypes.POINTER(_D), _P]),
+    "ebisu_plan_tune_share": (_I, [_P, _P, _P, _I64, _P, _I, _D, ctypes.POINTER(_D), _P]),
     "ebisu_plan_model": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_I), ctypes.POINTER(_D)]),
     "ebisu_cost_model": (_I, [ctypes.POINTER(ModelIn), ctypes.POINTER(ModelOut)]),
     "ebisu_reduce": (_I, [_P, _P, _P, ctypes.POINTER(_D), _P, _P]),
@@ -337,11 +338,18 @@ class Plan:
         s = current_stream_handle() if stream is None else stream
         return ebisu_sync(ctypes.c_void_p(ws.data_ptr()), s)
 
-    def tune(self, x, y, steps, ws, max_candidates=4):
+    def tune(self, x, y, steps, ws, max_candidates=4, share=1.0):
+        """Autotune on these buffers; `share` < 1: the plan will share the
+        GPU (a batch member), see ebisu_plan_tune_share."""
         a, b, w = self._ptrs(x, y, ws)
         best = _D()
-        _check(lib().ebisu_plan_tune(self.h, a, b, int(steps), w, int(max_candidates), ctypes.byref(best),
-                                     current_stream_handle()), "ebisu_plan_tune")
+        if share == 1.0:
+            rc = lib().ebisu_plan_tune(self.h, a, b, int(steps), w, int(max_candidates), ctypes.byref(best),
+                                       current_stream_handle())
+        else:
+            rc = lib().ebisu_plan_tune_share(self.h, a, b, int(steps), w, int(max_candidates), float(share),
+                                             ctypes.byref(best), current_stream_handle())
+        _check(rc, "ebisu_plan_tune")
         return best.value
 
     def reduce(self, a, ws, b=None):
