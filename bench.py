@@ -220,6 +220,8 @@ def run_case(args):
     plan = ebisu.Plan(nd, dims, shape, r, c, dt, ebisu.DIRICHLET)
     if args.params:
         plan.set_params(**{k: int(v) for k, v in (kv.split("=") for kv in args.params.split(","))})
+    if args.ablate:
+        plan.set_ablation(args.ablate)
     x = torch.from_numpy(g).to(ebisu.torch_dtype(dt)).cuda()
     y = torch.empty_like(x)
     ws = plan.workspace()
@@ -342,62 +344,73 @@ def run_paper_sizes(args):
                       "rows": rows}), flush=True)
 
 
+ABLATION_STEPS = [  # (label, ablation mask, deep?) -- the paper's cumulative breakdown (Section 7.4)
+    ("BASE: depth 1, shifting queues, no prefetch, barrier per level, one cell per thread", 15, False),
+    ("+CMQ: circular multi-queue, temporal depth t", 7, True),
+    ("+PRE: cp.async prefetch of input planes", 6, True),
+    ("+LST: lazy streaming, one barrier per plane", 4, True),
+    ("+RST: four cells per thread from registers (FP32)", 0, True),
+]
+
+
 def run_ablation(args):
-    """What each element of the design buys on this GPU, for the 2D 5-point
-    and 25-point stencils (8192^2) and the 3D 7-point star (512^3), FP32 and
-    FP64: the naive one-step kernel (no on-chip reuse); the shared-memory
-    kernel at depth 1 (tiles and prefetched plane rings, no temporal reuse);
-    the shared-memory kernel at depth 4 (plus temporal blocking with lazy
-    streaming, one barrier per plane); the register-streaming kernel at its
-    shallow and deep depth (queues in registers, no barrier).  Steps: 96
-    (2D) / 24 (3D); rows print as they finish."""
+    """The paper's performance breakdown (Section 7.4) measured on this GPU
+    for its two case studies, the 2D 5-point star (8192^2, 96 steps) and the
+    3D 7-point star (512^3, 24 steps), FP32 and FP64: the shared-memory
+    build with one more element switched on at each step (BASE, +CMQ, +PRE,
+    +LST, +RST; ebisu_plan_set_ablation), then the register-streaming build
+    (every level in registers, no barrier; beyond the paper), next to the
+    one-step kernel.  Fixed tiles (2D: 1024 columns x 108 rows; 3D: 64 x 32
+    columns x 103 planes), depth t = 4 (2D) / 3 (3D) from +CMQ on."""
     import torch
     from paper_2305_07390_gb300 import ebisu, synth
     stream = torch.cuda.current_stream()
     sh = ebisu.current_stream_handle()
     rows = []
-    cases = [("j2d5pt", 2, (8192, 8192), 0, 1, 96, dict(tile_x=1024, tile_s=108)),
-             ("j2d25pt", 2, (8192, 8192), 1, 2, 96, dict(tile_x=512, tile_s=108)),
-             ("j3d7pt", 3, (512, 512, 512), 0, 1, 24, dict(tile_x=64, tile_y=32, tile_s=103))]
-    for name, nd, dims, shape, r, steps, tb in cases:
-        g, c = synth.problem(nd, dims, shape, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED)
+    cases = [("j2d5pt", 2, (8192, 8192), 96, dict(tile_x=1024, tile_s=108), 4),
+             ("j3d7pt", 3, (512, 512, 512), 24, dict(tile_x=64, tile_y=32, tile_s=103), 3)]
+    for name, nd, dims, steps, tb, tdeep in cases:
+        g, c = synth.problem(nd, dims, 0, 1, synth.DIRICHLET, seed=synth.DEFAULT_SEED)
         cells = 1
         for d_ in dims:
             cells *= d_
         for dname, dt in (("f32", ebisu.F32), ("f64", ebisu.F64)):
-            plan = ebisu.Plan(nd, dims, shape, r, c, dt, ebisu.DIRICHLET)
+            plan = ebisu.Plan(nd, dims, 0, 1, c, dt, ebisu.DIRICHLET)
             x = torch.from_numpy(g).to(ebisu.torch_dtype(dt)).cuda()
             y = torch.empty_like(x)
             ws = plan.workspace()
-            lo, hi = plan.rs_depths()
-            variants = [("naive one-step kernel", None, True),
-                        ("shared memory, depth 1", dict(tb, depth=1, ctas_per_sm=2), False),
-                        ("shared memory, depth 4", dict(tb, depth=4, ctas_per_sm=2), False)]
-            for d in sorted({lo, hi} - {0}):
-                variants.append((f"register streaming, depth {d}",
-                                 dict(variant=2, depth=d, tile_s=128, ctas_per_sm=8), False))
-            for label, params, naive in variants:
-                try:
-                    if params is not None:
-                        plan.set_params(**params)
-                except ebisu.EbisuError:
-                    continue
+
+            def timed(naive=False):
                 plan.run(x, y, steps, ws, stream=sh, naive=naive)
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
                 plan.run(x, y, steps, ws, stream=sh, naive=naive)
                 b.record(stream)
                 b.synchronize()
-                rc = plan.sync(ws)
-                if rc != 0:
-                    continue
-                rate = cells * steps / (a.elapsed_time(b) * 1e-3)
-                rows.append({"stencil": name, "dtype": dname, "variant": label, "cell_updates_per_s": rate})
+                assert plan.sync(ws) == 0
+                return cells * steps / (a.elapsed_time(b) * 1e-3)
+
+            rows.append({"stencil": name, "dtype": dname, "step": "one-step kernel (no on-chip reuse)",
+                         "cell_updates_per_s": timed(naive=True)})
+            print(json.dumps(rows[-1]), flush=True)
+            for label, mask, deep in ABLATION_STEPS:
+                plan.set_ablation(0)
+                plan.set_params(**dict(tb, depth=tdeep if deep else 1, ctas_per_sm=2, variant=0))
+                plan.set_ablation(mask)
+                rows.append({"stencil": name, "dtype": dname, "step": label, "mask": mask,
+                             "depth": tdeep if deep else 1, "cell_updates_per_s": timed()})
+                print(json.dumps(rows[-1]), flush=True)
+            plan.set_ablation(0)
+            lo, hi = plan.rs_depths()
+            for d in sorted({lo, hi} - {0}):
+                plan.set_params(variant=2, depth=d, tile_s=128, ctas_per_sm=8)
+                rows.append({"stencil": name, "dtype": dname, "step": f"register streaming, depth {d}",
+                             "depth": d, "cell_updates_per_s": timed()})
                 print(json.dumps(rows[-1]), flush=True)
             del x, y, ws, plan
             torch.cuda.empty_cache()
-    print(json.dumps({"workload": "ablation of the design's elements (naive, shared-memory depth 1 and 4, "
-                                  "register streaming)", "rows": rows}), flush=True)
+    print(json.dumps({"workload": "the paper's performance breakdown (BASE, +CMQ, +PRE, +LST, +RST) on GB300, "
+                                  "then register streaming", "rows": rows}), flush=True)
 
 
 def npoints3(shape, r):
@@ -700,6 +713,7 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="--case: storage type")
     ap.add_argument("--params", default="", help="--case: plan parameters, k=v,k=v")
     ap.add_argument("--naive", action="store_true", help="--case: the one-step-per-launch kernel")
+    ap.add_argument("--ablate", type=int, default=0, help="--case: ablation mask of the shared-memory build")
     ap.add_argument("--workload", default="set", choices=["set", "set3d", "batch", "serve", "paper", "ablation"],
                     help="set: the FP64 2D stencil set (default, the headline line); set3d: the FP64 3D "
                          "set; batch: 512 uneven 2D 9-point box grids in one persistent launch per dtype; "

@@ -203,6 +203,33 @@ int ebisu_plan_set_params(ebisu_plan_t plan, const ebisu_params* p);
 int ebisu_plan_set_rounding(ebisu_plan_t plan, int rounding, uint64_t seed);
 int ebisu_plan_get_rounding(ebisu_plan_t plan, int* rounding, uint64_t* seed);
 
+/* Ablation of the shared-memory build (variant 0), to measure what each
+ * element of the method contributes -- the cumulative steps of the paper's
+ * performance breakdown (Section 7.4: BASE, +CMQ, +PRE, +LST, +RST):
+ *   EBISU_ABLATE_REGISTER_REUSE : FP32 cells one per thread from shared
+ *                                 memory (no four-cells-per-thread reuse in
+ *                                 registers; FP64 already works this way);
+ *   EBISU_ABLATE_LAZY           : a barrier after every level, level s
+ *                                 lagging level s-1 by r planes (instead of
+ *                                 lag r+1 and one barrier per plane);
+ *   EBISU_ABLATE_PREFETCH       : each input plane loaded and waited for in
+ *                                 the iteration that uses it;
+ *   EBISU_ABLATE_CIRCULAR       : queues that shift down one slot per plane
+ *                                 by copying, instead of circular indexing.
+ * mask must be a cumulative step: 0 (everything on), REGISTER_REUSE,
+ * REGISTER_REUSE|LAZY, REGISTER_REUSE|LAZY|PREFETCH, or all four
+ * (EBISU_ERR_INVALID_ARG otherwise).  Built for the two case-study stencils
+ * only: the 2D 5-point and 3D 7-point star (radius 1), FP32 and FP64
+ * storage (EBISU_ERR_UNSUPPORTED otherwise).  Results are unchanged (the
+ * same FMA chains); only the speed differs.  Host only. */
+enum ebisu_ablate {
+    EBISU_ABLATE_PREFETCH = 1,
+    EBISU_ABLATE_LAZY = 2,
+    EBISU_ABLATE_REGISTER_REUSE = 4,
+    EBISU_ABLATE_CIRCULAR = 8
+};
+int ebisu_plan_set_ablation(ebisu_plan_t plan, int mask);
+
 /* Temporal depths built for the register-streaming kernel (variant 2) of
  * this plan's stencil and storage type (Section 4's temporal blocking with
  * the per-level queues held in registers): *shallow <= *deep.  3D plans: 1

@@ -181,16 +181,9 @@ int layout(ebisu_batch_s* b)
             g.smem = std::max(g.smem, tb_smem_bytes(&b->plans[m], q));
             g.plane_cap = std::max<int>(g.plane_cap, (int)plane_capacity(&b->plans[m], q));
         }
-        // the ring layout uses the group's largest plane for every member:
-        // recompute the shared memory with that stride
-        size_t need = 0;
-        for (int m : g.members) {
-            const ebisu_plan_s* p = &b->plans[m];
-            const int d = (int)std::min<int64_t>(p->prm.depth, b->steps[m]);
-            const size_t slots = (size_t)ring_q0(p->radius, p->ndim, g.variant, p->esize) + (size_t)(d - 1) * ring_q(p->radius);
-            need = std::max(need, slots * (size_t)g.plane_cap * p->esize);
-        }
-        g.smem = need;
+        // every member lays its rings out with its own plane stride (its
+        // descriptor carries it), so the launch needs the largest member's
+        // footprint, which fits because each member's parameters were checked
         if (g.smem + 4096 > device_info().smem_optin) return EBISU_ERR_UNSUPPORTED;
     }
     b->grid_off.assign(n, 0);
@@ -275,6 +268,9 @@ int ebisu_batch_create(int n, const ebisu_plan_t* plans, const void* const* in, 
             } else {
                 fill_grid_desc(p, b->in[m], b->out[m], wsg, b->steps[m], b->copy_in[m], &b->descs[m]);
                 b->descs[m].grid_id = (int32_t)k;
+                ebisu_params q = p->prm;
+                q.depth = (int)std::min<int64_t>(q.depth, b->steps[m]);
+                b->descs[m].plane_cap = (int32_t)plane_capacity(p, q);
             }
         }
     }

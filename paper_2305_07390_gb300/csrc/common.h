@@ -43,6 +43,9 @@ struct GridDesc {
     int32_t grid_id;     // index into Control::done
     int32_t load_mode;   // 0 = element cp.async, 1 = pair cp.async (2-byte
                          // types, rows of a plane share parity), 2 = staged
+    int32_t plane_cap;   // elements per ring plane of this problem (its own
+                         // stride, so batch members need no common one)
+    int32_t reserved_;
     int64_t total_elems; // stored elements of the grid (bounds of pair loads)
     double coef[kMaxPoints];
 };

@@ -42,7 +42,8 @@ struct PadParams {
 #define EBISU_DECLARE_RS_PTRS(NAME)                                \
     const void* rs_ptr_##NAME##_0(int shape, int r, int depth);    \
     const void* rs_ptr_##NAME##_1(int shape, int r, int depth);    \
-    const void* rs3_ptr_##NAME(int shape, int r, int depth);
+    const void* rs3_ptr_##NAME##_0(int shape, int r, int depth);   \
+    const void* rs3_ptr_##NAME##_1(int shape, int r, int depth);
 
 EBISU_DECLARE_RS_PTRS(f64)
 EBISU_DECLARE_RS_PTRS(f32)
@@ -67,6 +68,12 @@ cudaError_t naive_launch_bf16sr(int d, int s, int r, const void* a, void* b, con
 EBISU_DECLARE_DTYPE_ENTRY(f64)
 EBISU_DECLARE_DTYPE_ENTRY(f32)
 EBISU_DECLARE_DTYPE_ENTRY(bf16)
+
+// kern_ablate.cu: ablation builds of the shared-memory kernel (2D 5-point
+// and 3D 7-point star, FP32/FP64; mask = the tb_kernel.cuh kAbl* bits)
+cudaError_t tb_ablate_launch(size_t esize, int dim, int mask, const TBParams& p, int grid, size_t smem,
+                             cudaStream_t st);
+cudaError_t tb_ablate_occupancy(size_t esize, int dim, int mask, size_t smem, int* blocks);
 
 // util.cu
 cudaError_t reduce_final(const double* part, int64_t nparts, double* out3_dev, cudaStream_t st);

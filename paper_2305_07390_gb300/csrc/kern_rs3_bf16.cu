@@ -1,4 +1,4 @@
 // Register-streaming 3D kernels for BF16 storage.
 #define EBISU_RS3D_KERNELS
 #include "rs_impl.cuh"
-EBISU_DEFINE_RS3D_PTRS(__nv_bfloat16, bf16)
+EBISU_DEFINE_RS3D_PTRS(__nv_bfloat16, bf16, 0)

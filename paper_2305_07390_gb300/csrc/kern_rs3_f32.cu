@@ -1,4 +1,4 @@
 // Register-streaming 3D kernels for FP32 storage.
 #define EBISU_RS3D_KERNELS
 #include "rs_impl.cuh"
-EBISU_DEFINE_RS3D_PTRS(float, f32)
+EBISU_DEFINE_RS3D_PTRS(float, f32, 0)

@@ -786,6 +786,23 @@ int ebisu_plan_set_rounding(ebisu_plan_t plan, int rounding, uint64_t seed)
     return EBISU_OK;
 }
 
+int ebisu_plan_set_ablation(ebisu_plan_t plan, int mask)
+{
+    if (!plan) return EBISU_ERR_INVALID_ARG;
+    const int steps[] = {0, EBISU_ABLATE_REGISTER_REUSE, EBISU_ABLATE_REGISTER_REUSE | EBISU_ABLATE_LAZY,
+                         EBISU_ABLATE_REGISTER_REUSE | EBISU_ABLATE_LAZY | EBISU_ABLATE_PREFETCH,
+                         EBISU_ABLATE_REGISTER_REUSE | EBISU_ABLATE_LAZY | EBISU_ABLATE_PREFETCH |
+                             EBISU_ABLATE_CIRCULAR};
+    bool known = false;
+    for (int m : steps) known = known || (m == mask);
+    if (!known) return EBISU_ERR_INVALID_ARG;
+    if (mask != 0 && (plan->shape != EBISU_STAR || plan->radius != 1 || plan->dtype == EBISU_BF16 ||
+                      plan_sr(plan)))
+        return EBISU_ERR_UNSUPPORTED;
+    plan->ablate = mask;
+    return EBISU_OK;
+}
+
 int ebisu_plan_get_rounding(ebisu_plan_t plan, int* rounding, uint64_t* seed)
 {
     if (!plan || !rounding) return EBISU_ERR_INVALID_ARG;
@@ -876,16 +893,19 @@ static int run_common(ebisu_plan_t p, const void* in, void* out, int64_t steps, 
     ebisu_params qd = q;
     qd.depth = d;
     prm.smem_plane = (int32_t)plane_capacity(p, qd);
+    prm.g.plane_cap = prm.smem_plane;
     const size_t smem = tb_smem_bytes(p, qd);
     const int variant = kernel_variant(p->dtype, q.ctas_per_sm);
     int occ = 0;
-    e = tb_occupancy(p, variant, smem, &occ);
+    e = p->ablate ? tb_ablate_occupancy(p->esize, p->ndim, p->ablate, smem, &occ)
+                  : tb_occupancy(p, variant, smem, &occ);
     if (e != cudaSuccess) return fail_cuda(e);
     if (occ < 1) return EBISU_ERR_UNSUPPORTED;
     const DeviceInfo& dv = device_info();
     int64_t grid = (int64_t)std::min(occ, q.ctas_per_sm) * dv.sms;
     grid = std::min<int64_t>(grid, prm.nitems);
-    e = tb_launch(p, variant, prm, (int)grid, smem, st);
+    e = p->ablate ? tb_ablate_launch(p->esize, p->ndim, p->ablate, prm, (int)grid, smem, st)
+                  : tb_launch(p, variant, prm, (int)grid, smem, st);
     if (e != cudaSuccess) return fail_cuda(e);
     return EBISU_OK;
 }

@@ -28,6 +28,7 @@ struct ebisu_plan_s {
     int rounding = 0;
     uint64_t sr_seed = 0;
     uint32_t sr_key = 0;
+    int ablate = 0;  // shared-memory build with elements switched off (EBISU_ABLATE_* mask)
 };
 
 namespace ebisu {

@@ -54,27 +54,37 @@ static const void* rs_ptr_pick(int depth)
 
 #include "rs3_kernel.cuh"
 #include "rs3t_kernel.cuh"
-// defines rs3_ptr_<NAME>(shape, r, depth): FP64 at depth 1 (the 7- and
-// 13-point stars and the 27-point box); FP32 and BF16 radius 1: the 7-point
-// star at depth 2 or 3, the 27-point box at depth 2
-#define EBISU_DEFINE_RS3D_PTRS(T, NAME)                                                                \
+// defines rs3_ptr_<NAME>_<PART>(shape, r, depth), the 3D kernels of one
+// storage type split over two translation units so that they compile in
+// parallel: part 0 the stars and the 27-point box, part 1 poisson and
+// j3d17pt.  FP64 at depth 1 (the 7- and 13-point stars, the three radius-1
+// boxes); FP32 and BF16 radius 1: the 7-point star at depth 2 or 3, the
+// others at depth 2.
+#define EBISU_DEFINE_RS3D_PTRS(T, NAME, PART)                                                          \
     namespace ebisu {                                                                                  \
-    const void* rs3_ptr_##NAME(int shape, int r, int depth)                                            \
+    const void* rs3_ptr_##NAME##_##PART(int shape, int r, int depth)                                   \
     {                                                                                                  \
-        if constexpr (sizeof(T) == 8) {                                                                \
-            if (depth != 1) return nullptr;                                                            \
-            if (shape == kStar && r == 1) return (const void*)&rs3_kernel<T, kStar, 1>;                \
-            if (shape == kStar && r == 2) return (const void*)&rs3_kernel<T, kStar, 2>;                \
-            if (shape == kBox && r == 1) return (const void*)&rs3_kernel<T, kBox, 1>;                  \
-            if (shape == kPoisson && r == 1) return (const void*)&rs3_kernel<T, kPoisson, 1>;          \
-            if (shape == kJ3d17 && r == 1) return (const void*)&rs3_kernel<T, kJ3d17, 1>;              \
+        if constexpr (PART == 0) {                                                                     \
+            if constexpr (sizeof(T) == 8) {                                                            \
+                if (depth != 1) return nullptr;                                                        \
+                if (shape == kStar && r == 1) return (const void*)&rs3_kernel<T, kStar, 1>;            \
+                if (shape == kStar && r == 2) return (const void*)&rs3_kernel<T, kStar, 2>;            \
+                if (shape == kBox && r == 1) return (const void*)&rs3_kernel<T, kBox, 1>;              \
+            } else {                                                                                   \
+                if (r == 1 && shape == kStar && depth == 2) return (const void*)&rs3t_kernel<T, kStar, 2>; \
+                if (r == 1 && shape == kStar && depth == 3) return (const void*)&rs3t_kernel<T, kStar, 3>; \
+                if (r == 1 && shape == kBox && depth == 2) return (const void*)&rs3t_kernel<T, kBox, 2>; \
+            }                                                                                          \
         } else {                                                                                       \
-            if (r == 1 && shape == kStar && depth == 2) return (const void*)&rs3t_kernel<T, kStar, 2>; \
-            if (r == 1 && shape == kStar && depth == 3) return (const void*)&rs3t_kernel<T, kStar, 3>; \
-            if (r == 1 && shape == kBox && depth == 2) return (const void*)&rs3t_kernel<T, kBox, 2>;   \
-            if (r == 1 && shape == kPoisson && depth == 2)                                             \
-                return (const void*)&rs3t_kernel<T, kPoisson, 2>;                                      \
-            if (r == 1 && shape == kJ3d17 && depth == 2) return (const void*)&rs3t_kernel<T, kJ3d17, 2>; \
+            if constexpr (sizeof(T) == 8) {                                                            \
+                if (depth != 1) return nullptr;                                                        \
+                if (shape == kPoisson && r == 1) return (const void*)&rs3_kernel<T, kPoisson, 1>;      \
+                if (shape == kJ3d17 && r == 1) return (const void*)&rs3_kernel<T, kJ3d17, 1>;          \
+            } else {                                                                                   \
+                if (r == 1 && shape == kPoisson && depth == 2)                                         \
+                    return (const void*)&rs3t_kernel<T, kPoisson, 2>;                                  \
+                if (r == 1 && shape == kJ3d17 && depth == 2) return (const void*)&rs3t_kernel<T, kJ3d17, 2>; \
+            }                                                                                          \
         }                                                                                              \
         (void)shape; (void)r; (void)depth;                                                             \
         return nullptr;                                                                                \
@@ -101,6 +111,11 @@ static const void* rs_ptr_pick(int depth)
         const void* k = rs_ptr_##NAME(s, r, d, bt);                                                      \
         if (!k) return cudaErrorInvalidValue;                                                            \
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, k, kRSThreads, 0);                       \
+    }                                                                                                    \
+    static const void* rs3_ptr_##NAME(int s, int r, int d)                                               \
+    {                                                                                                    \
+        const void* k = rs3_ptr_##NAME##_0(s, r, d);                                                     \
+        return k ? k : rs3_ptr_##NAME##_1(s, r, d);                                                      \
     }                                                                                                    \
     cudaError_t rs3_launch_##NAME(int s, int r, int d, const RS3Params& p, int g, cudaStream_t st)       \
     {                                                                                                    \

@@ -50,12 +50,15 @@ struct RSGeom {
     static constexpr int U = 2 * R + 1;                       // rows queued per level
     static constexpr bool EXT = (SHAPE == kBox);              // rows stored with halo
     static constexpr int RW = EXT ? 4 + 2 * R : 4;            // values per queued row
-    // Level-0 rows in flight.  FP32/FP64 storage: PFS rows staged in shared
-    // memory by cp.async (each lane copies and later reads back only its own
-    // columns, so no barrier is needed).  BF16 (2-byte elements, below
-    // cp.async's 4-byte minimum) and the 25-point box (measured faster
-    // with its 5 rows in registers): PF rows in registers (PF divides U).
-    static constexpr bool ASYNC = sizeof(T) >= 4 && !(EXT && R == 2);
+    // Level-0 rows in flight.  PFS rows staged in shared memory by cp.async
+    // (each lane copies and later reads back only its own columns, so no
+    // barrier is needed).  2-byte storage is below cp.async's 4-byte
+    // minimum, so a BF16 lane copies the 4-byte-aligned pairs covering its
+    // columns (one pair more than it needs) and reads back from the row's
+    // parity.  The 25-point box (measured faster with its 5 rows in
+    // registers): PF rows in registers (PF divides U).
+    static constexpr bool ASYNC = !(EXT && R == 2);
+    static constexpr int SW = (sizeof(T) == 2) ? RW + 2 : RW;  // elements of a lane's staging slot
     static constexpr int PFS = (sizeof(T) == 8) ? 4 : 8;
     static constexpr int PF = ASYNC ? 1 : ((sizeof(C) == 8) ? 1 : U);
     static constexpr int WORDS = (int)sizeof(C) / 4;
@@ -125,8 +128,9 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
     C ring[D][U][RW];                 // levels 0 .. D-1; level D goes to global memory
     C stage[ASYNC ? 1 : PF][RW];      // level-0 rows in flight (registers)
     // level-0 rows in flight (shared memory): [warp][slot][lane][column]
-    __shared__ __align__(16) T s_stage[ASYNC ? kRSWarps * PFS * 32 * RW : 1];
-    T* const my_stage = s_stage + (ASYNC ? ((threadIdx.x >> 5) * PFS * 32 + lane) * RW : 0);
+    constexpr int SW = G::SW;
+    __shared__ __align__(16) T s_stage[ASYNC ? kRSWarps * PFS * 32 * SW : 1];
+    T* const my_stage = s_stage + (ASYNC ? ((threadIdx.x >> 5) * PFS * 32 + lane) * SW : 0);
 
     for (;;) {
         // ---- pop an item: (problem, temporal block, tile) ---------------------
@@ -278,7 +282,9 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
         bool general = true;
         if constexpr (kLean) {
             const bool lane_edge = per ? !contig : (padm != 0u || lvm != (1u << RW) - 1u);
-            general = __any_sync(FULL, lane_edge) || lastb || (!per && (ya - R * D < 0 || yb + R * D > n0i));
+            // (the last block needs the pass-through copies only when it is shallower)
+            general = __any_sync(FULL, lane_edge) || (lastb && gd->depth_last < D) ||
+                      (!per && (ya - R * D < 0 || yb + R * D > n0i));
         }
 
         // level-0 row y (general loop: rows past the loaded region are
@@ -309,12 +315,50 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
         // lane's slot by cp.async (zero-filled where the column does not
         // exist); rows past the loaded region are skipped (general loop) or
         // clamped into it (lean loop).  One commit group per row, always.
+        // 2-byte storage: the first stored element of this lane's columns in
+        // row y (periodic: wrapped; only for lanes without a wrap inside)
+        auto elem0 = [&](int y) -> int64_t {
+            if (per) {
+                const int yw = (y < 0) ? y + n0i : (y >= n0i ? y - n0i : y);
+                return (int64_t)yw * lds + cw0;
+            }
+            return (int64_t)(y + pad) * lds + (c0 + pad);
+        };
+        const int64_t total = (int64_t)(n0i + 2 * pad) * lds;  // stored elements of the grid
         auto issue_row = [&](int slot, int y, const bool G, const bool lean) {
-            T* const sp = my_stage + slot * (32 * RW);
+            T* const sp = my_stage + slot * (32 * SW);
             bool skip = false;
             if (lean) y = min(y, hi0 - 1);
             else skip = (y >= hi0);
-            if (!skip) {
+            if (!skip && sizeof(T) == 2) {
+                if (per && G && !contig) {
+                    // a wrap inside the lane's columns: element loads into the slot
+                    const int yw = (y < 0) ? y + n0i : (y >= n0i ? y - n0i : y);
+                    const T* rp = src + (int64_t)yw * lds;
+#pragma unroll
+                    for (int q = 0; q < RW; ++q) {
+                        const int c = cw0 + q;
+                        sp[q] = Dt::raw(rp + (c >= n2 ? c - n2 : c));
+                    }
+                } else {
+                    // the pairs [a, a + SW) with a the element below the first
+                    // column rounded down to even; pairs outside the array are
+                    // zero-filled (their cells lie outside the padded row), and
+                    // an odd-sized array's last element, whose pair would end
+                    // past the array, is copied alone
+                    const int64_t a = elem0(y) & ~(int64_t)1;
+#pragma unroll
+                    for (int q = 0; q < SW; q += 2) {
+                        const int64_t e = a + q;
+                        const bool ok = e >= 0 && e + 1 < total;
+                        if (!ok && e >= 0 && e < total) {
+                            sp[q] = Dt::raw(src + e);
+                        } else {
+                            rs_cp_async<4>(sp + q, ok ? src + e : src, ok ? 4 : 0);
+                        }
+                    }
+                }
+            } else if (!skip) {
                 if (per) {
                     const int yw = (y < 0) ? y + n0i : (y >= n0i ? y - n0i : y);
                     const T* rp = src + (int64_t)yw * lds;
@@ -335,11 +379,39 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
             rs_cp_commit();
         };
         // the oldest row in flight into level 0's queue slot u
-        auto take_row = [&](int u, int slot) {
+        auto take_row = [&](int u, int slot, int y, const bool G, const bool lean) {
             rs_cp_wait<PFS - 1>();
-            const T* const sp = my_stage + slot * (32 * RW);
+            const T* const sp = my_stage + slot * (32 * SW);
+            // a lane's slot starts on a multiple of RW elements: 16-byte
+            // loads for four floats (or two doubles), 8-byte loads for pairs
+            if constexpr (sizeof(T) == 2) {
+                // the row's parity (the same clamp as when it was issued)
+                if (lean) y = min(y, hi0 - 1);
+                const int par = (per && G && !contig) ? 0 : (int)(elem0(y) & 1);
+                const unsigned short* const s16 = reinterpret_cast<const unsigned short*>(sp) + par;
 #pragma unroll
-            for (int q = 0; q < RW; ++q) ring[0][u][q] = Dt::widen(sp[q]);
+                for (int q = 0; q < RW; ++q) ring[0][u][q] = __uint_as_float((unsigned)s16[q] << 16);
+            } else if constexpr (sizeof(T) == 4 && RW % 4 == 0) {
+#pragma unroll
+                for (int q = 0; q < RW; q += 4) {
+                    const float4 v = *reinterpret_cast<const float4*>(sp + q);
+                    ring[0][u][q] = v.x;
+                    ring[0][u][q + 1] = v.y;
+                    ring[0][u][q + 2] = v.z;
+                    ring[0][u][q + 3] = v.w;
+                }
+            } else if constexpr ((sizeof(T) == 4 || sizeof(T) == 8) && RW % 2 == 0) {
+                using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+#pragma unroll
+                for (int q = 0; q < RW; q += 2) {
+                    const V2 v = *reinterpret_cast<const V2*>(sp + q);
+                    ring[0][u][q] = v.x;
+                    ring[0][u][q + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < RW; ++q) ring[0][u][q] = Dt::widen(sp[q]);
+            }
         };
 
         // One level's row, split in two parts of the canonical FMA chain:
@@ -384,6 +456,23 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                 return Dt::widen(Dt::narrow(a));
             }
         };
+        // a level's four results rounded (BF16 to nearest: two packed
+        // conversions, each element rounded on its own as by one conversion)
+        auto round_row = [&](int s, int y, int cs, C(&o)[4]) {
+            if constexpr (!Dt::kSR && sizeof(T) == 2) {
+#pragma unroll
+                for (int q2 = 0; q2 < 2; ++q2) {
+                    const __nv_bfloat162 p = __floats2bfloat162_rn(acc_ref(s, cs, 2 * q2), acc_ref(s, cs, 2 * q2 + 1));
+                    const unsigned w = *reinterpret_cast<const unsigned*>(&p);
+                    o[2 * q2] = __uint_as_float(w << 16);
+                    o[2 * q2 + 1] = __uint_as_float(w & 0xffff0000u);
+                }
+            } else {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) o[m] = round_cell(s, y, m, acc_ref(s, cs, m));
+            }
+        };
+
         auto level_row = [&](int s, int cs, const bool head) {
             C e[EXT ? 1 : 4 + 2 * R];
             if (!EXT && head) {
@@ -505,7 +594,7 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                         const int yi = lo0 + j0 + u;  // level-0 row arriving now
                         if constexpr (ASYNC) {
                             const int slot = (j0 + u) & (PFS - 1);
-                            take_row(u, slot);
+                            take_row(u, slot, yi, G, true);
                             issue_row(slot, yi + PFS, G, true);
                         } else {
 #pragma unroll
@@ -520,16 +609,13 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                             const int cs = ((u - s * R) % U + U) % U;  // queue slot of row y
                             C o[4];
                             level_row(s, cs, false);
+                            round_row(s, y, cs, o);
                             if constexpr (G) {
                                 const bool copy = (s > deff) || (!per && (y < 0 || y >= n0i));
                                 const unsigned keep = copy ? 0xfu : padm;
 #pragma unroll
                                 for (int m = 0; m < 4; ++m)
-                                    o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m]
-                                                              : round_cell(s, y, m, acc_ref(s, cs, m));
-                            } else {
-#pragma unroll
-                                for (int m = 0; m < 4; ++m) o[m] = round_cell(s, y, m, acc_ref(s, cs, m));
+                                    if ((keep >> m) & 1u) o[m] = ring[s - 1][cs][X0 + m];
                             }
                             put_row(s, cs, y, o);
                         }
@@ -554,7 +640,7 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                     const int yi = lo0 + j0 + u;  // level-0 row arriving now
                     if constexpr (ASYNC) {
                         const int slot = (j0 + u) & (PFS - 1);
-                        take_row(u, slot);
+                        take_row(u, slot, yi, true, false);
                         issue_row(slot, yi + PFS, true, false);
                     } else {
 #pragma unroll
@@ -573,9 +659,10 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                         const unsigned keep = copy ? 0xfu : padm;
                         C o[4];
                         level_row(s, cs, false);
+                        round_row(s, y, cs, o);
 #pragma unroll
                         for (int m = 0; m < 4; ++m)
-                            o[m] = ((keep >> m) & 1u) ? ring[s - 1][cs][X0 + m] : round_cell(s, y, m, acc_ref(s, cs, m));
+                            if ((keep >> m) & 1u) o[m] = ring[s - 1][cs][X0 + m];
                         put_row(s, cs, y, o);
                     }
                 }

@@ -130,7 +130,20 @@ __device__ __forceinline__ void store_quad(double* p, const double* v)
 // may start up to 4 columns left of a row without leaving the slot.
 constexpr int kRingMargin = 4;
 
-template <class T, int DIM, int SHAPE, int R, int NT, int ILP, int PF, int STG, int MINB, int VEC>
+// Ablation builds (the paper's Section 7.4 breakdown, measured one element
+// at a time; ABL = 0 in every production build):
+//   kAblNoPrefetch : each input plane is loaded and waited for in the
+//                    iteration that uses it (no planes in flight ahead);
+//   kAblNoLazy     : level s lags level s-1 by r planes, one barrier after
+//                    every level (instead of lag r+1, one barrier per plane);
+//   kAblNoRegReuse : FP32/BF16 compute one cell per thread from shared
+//                    memory (no four-cells-per-thread register reuse);
+//   kAblNoCircular : every queue shifts down one slot per streamed plane by
+//                    copying (instead of circular indexing); implies the two
+//                    above, the state the queue is introduced in.
+enum { kAblNoPrefetch = 1, kAblNoLazy = 2, kAblNoRegReuse = 4, kAblNoCircular = 8 };
+
+template <class T, int DIM, int SHAPE, int R, int NT, int ILP, int PF, int STG, int MINB, int VEC, int ABL = 0>
 __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TBParams prm)
 {
     using St = Stencil<DIM, SHAPE, R>;
@@ -145,7 +158,11 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
     constexpr auto OFF = St::kOff;
     constexpr auto ROWS = St::make_rows();
     // 4-wide path (chosen per storage type by the build, see kernels_impl.cuh)
-    constexpr bool kVec = (VEC != 0);
+    constexpr bool kVec = (VEC != 0) && !(ABL & kAblNoRegReuse);
+    constexpr bool kShift = (ABL & kAblNoCircular) != 0;
+    constexpr bool kNoPF = kShift || (ABL & kAblNoPrefetch) != 0;
+    constexpr bool kNoLazy = kShift || (ABL & kAblNoLazy) != 0;
+    static_assert(ABL == 0 || sizeof(T) >= 4, "ablation builds: 4- and 8-byte storage");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const ring = reinterpret_cast<T*>(smem_raw);
@@ -155,7 +172,6 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
 
     const int tid = threadIdx.x;
     Control* const ctl = prm.ctl;
-    const int plane_cap = prm.smem_plane;
 
     for (;;) {
         // ---- pop the next work item ---------------------------------------
@@ -222,6 +238,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
         if (!s_cmd[0]) return;
 
         // ---- geometry of this item ------------------------------------------
+        const int plane_cap = sg.plane_cap > 0 ? sg.plane_cap : prm.smem_plane;  // ring plane stride
         const bool last = (blk == sg.nblocks - 1);
         const int d = last ? sg.last_depth : sg.depth;
         const bool dst_is_out = ((sg.nblocks - 1 - blk) % 2) == 0;
@@ -292,8 +309,21 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             }
             return (int64_t)(q1 + pad1) * ld1 + (q2 + pad);
         };
+        // plane of level s streamed at iteration j is slo0 + j - lag(s)
+        auto lag = [&](int s) -> int64_t {
+            if constexpr (kNoLazy) return (int64_t)R * s;
+            return s == 0 ? 0 : (int64_t)R + (int64_t)(s - 1) * (R + 1);
+        };
+        int64_t jcur = 0;  // the streaming iteration (shifting queues only)
         // ring slot of plane ps at level lev (0 = input ring)
         auto ring_plane = [&](int lev, int64_t ps) -> T* {
+            if constexpr (kShift) {
+                // the newest plane of a level sits in its last slot
+                const int qq = (lev == 0) ? Q0 : Q;
+                const int slot = qq - 1 - (int)(slo0 + jcur - lag(lev) - ps);
+                if (lev == 0) return ring + (size_t)slot * plane_cap + kRingMargin;
+                return ring + ((size_t)Q0 + (size_t)(lev - 1) * Q + slot) * plane_cap + kRingMargin;
+            }
             const unsigned rel = (unsigned)(ps - slo0);
             if (lev == 0) return ring + (size_t)(rel % Q0) * plane_cap + kRingMargin;
             return ring + ((size_t)Q0 + (size_t)(lev - 1) * Q + (rel % Q)) * plane_cap + kRingMargin;
@@ -597,10 +627,41 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
         };
 
         // ---- stream the tile ----------------------------------------------------
-        auto lag = [&](int s) -> int64_t { return (int64_t)R + (int64_t)(s - 1) * (R + 1); };
         const int64_t lastp = bs - 1;  // last plane of level d
         const int64_t niter = lastp - slo0 + lag(d) + 1;
-        if (mode != kLoadStaged) {
+        if constexpr (kNoPF) {
+            // ablation: planes are loaded in the iteration that uses them
+#pragma unroll 1
+            for (int64_t j = 0; j < niter; ++j) {
+                jcur = j;
+                const int64_t pcur = slo0 + j;
+                if (pcur < shi0) issue_plane(pcur);
+                cp_async_commit();
+                cp_async_wait<0>();
+                __syncthreads();
+                for (int s = 1; s <= d; ++s) {
+                    const int64_t ps = slo0 + j - lag(s);
+                    if (ps >= lo_s(as, R, s, pad) && ps < hi_s(bs, n0, R, s, pad)) {
+                        if constexpr (kVec)
+                            compute_plane_vec(s, ps);
+                        else
+                            compute_plane(s, ps);
+                    }
+                    if (kNoLazy && s < d) __syncthreads();
+                }
+                if constexpr (kShift) {
+                    // every queue moves down one slot (slot k+1 -> k)
+                    __syncthreads();
+                    for (int lev = 0; lev < d; ++lev) {
+                        const int qq = (lev == 0) ? Q0 : Q;
+                        T* const base = (lev == 0) ? ring : ring + ((size_t)Q0 + (size_t)(lev - 1) * Q) * plane_cap;
+                        for (int i = tid; i < plane_cap; i += NT)
+                            for (int k = 0; k + 1 < qq; ++k) base[(size_t)k * plane_cap + i] = base[(size_t)(k + 1) * plane_cap + i];
+                    }
+                }
+                __syncthreads();
+            }
+        } else if (mode != kLoadStaged) {
             // prologue: PF planes in flight, one commit group each
 #pragma unroll 1
             for (int k = 0; k < PF; ++k) {
@@ -611,7 +672,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
             issue_plane(slo0);
             finish_staged(slo0);
         }
-        for (int64_t j = 0; j < niter; ++j) {
+        for (int64_t j = 0; j < (kNoPF ? 0 : niter); ++j) {
             if (mode != kLoadStaged) cp_async_wait<PF - 1>();
             __syncthreads();
             const int64_t pnext = slo0 + j + ((mode != kLoadStaged) ? PF : 1);
@@ -630,6 +691,7 @@ __global__ void __launch_bounds__(NT, MINB) tb_kernel(const __grid_constant__ TB
                     else
                         compute_plane(s, ps);
                 }
+                if (kNoLazy && s < d) __syncthreads();  // ablation: a barrier per level
             }
             if (mode == kLoadStaged && have_next) finish_staged(pnext);
         }

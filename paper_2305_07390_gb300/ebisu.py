@@ -25,6 +25,7 @@ F64, F32, BF16 = 0, 1, 2
 DIRICHLET, PERIODIC = 0, 1
 ROUND_NEAREST, ROUND_STOCHASTIC = 0, 1
 SERVE_FIFO, SERVE_SHORTEST = 0, 1
+ABLATE_PREFETCH, ABLATE_LAZY, ABLATE_REGISTER_REUSE, ABLATE_CIRCULAR = 1, 2, 4, 8
 
 
 class EbisuError(RuntimeError):
@@ -82,6 +83,7 @@ SIGNATURES = {
     "ebisu_plan_set_params": (_I, [_P, ctypes.POINTER(Params)]),
     "ebisu_plan_rs_depths": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "ebisu_plan_set_rounding": (_I, [_P, _I, ctypes.c_uint64]),
+    "ebisu_plan_set_ablation": (_I, [_P, _I]),
     "ebisu_plan_get_rounding": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_uint64)]),
     "ebisu_plan_workspace_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "ebisu_run": (_I, [_P, _P, _P, _I64, _P, _P]),
@@ -295,6 +297,10 @@ class Plan:
         """Storage rounding: ROUND_NEAREST or (BF16 only) ROUND_STOCHASTIC."""
         _check(lib().ebisu_plan_set_rounding(self.h, int(rounding), ctypes.c_uint64(int(seed))),
                "ebisu_plan_set_rounding")
+
+    def set_ablation(self, mask):
+        """Switch elements of the shared-memory build off (EBISU_ABLATE_* mask)."""
+        _check(lib().ebisu_plan_set_ablation(self.h, int(mask)), "ebisu_plan_set_ablation")
 
     def rounding(self):
         r, sd = _I(), ctypes.c_uint64()

@@ -224,3 +224,21 @@ def test_new_shapes_and_offset_lists_host_rules():
     with pytest.raises(ebisu.EbisuError) as ei:
         ebisu.Plan.from_offsets(2, (40, 40), [(0, 3, 1), (0, 0, 0)], [0.5, 0.5])  # radius 3, not a star
     assert ei.value.code == ebisu.ERR_UNSUPPORTED
+
+
+def test_ablation_host_rules():
+    p = ebisu.Plan(2, (64, 300), 0, 1, [0.2] * 5, ebisu.F32, 0)
+    steps = [0, 4, 6, 7, 15]
+    for m in steps:
+        p.set_ablation(m)
+    for bad in (1, 2, 3, 8, 16):
+        with pytest.raises(ebisu.EbisuError) as ei:
+            p.set_ablation(bad)
+        assert ei.value.code == ebisu.ERR_INVALID_ARG
+    for args in [(2, (64, 300), 1, 1, [1 / 9] * 9, ebisu.F32), (2, (64, 300), 0, 2, [1 / 9] * 9, ebisu.F64),
+                 (2, (64, 300), 0, 1, [0.2] * 5, ebisu.BF16)]:
+        q = ebisu.Plan(2, args[1], args[2], args[3], args[4], args[5], 0)
+        with pytest.raises(ebisu.EbisuError) as ei:
+            q.set_ablation(15)
+        assert ei.value.code == ebisu.ERR_UNSUPPORTED
+        q.set_ablation(0)

@@ -258,3 +258,21 @@ def test_serve_shortest_first_and_wait_limit():
         assert rc in (eb.OK, eb.ERR_BUSY)
     srv.close()
     assert srv.h is None
+
+
+def test_batch_members_with_different_ring_footprints():
+    """A wide shallow member and a narrow deep member of one shared-memory
+    group: each lays its rings out with its own plane stride, so the group
+    needs the larger single footprint, not the widest plane times the
+    deepest ring."""
+    eb = _eb()
+    a = make_problem(eb, 2, (300, 3000), 1, 1, eb.F64, 0, 71, dict(tile_x=3000, tile_s=60, depth=1))
+    b = make_problem(eb, 2, (300, 600), 1, 1, eb.F64, 0, 72, dict(tile_x=512, tile_s=60, depth=12))
+    plans, xs = [a[0], b[0]], [a[1], b[1]]
+    ys = [torch.empty_like(x) for x in xs]
+    steps = [7, 30]
+    ws = torch.empty(eb.batch_workspace_bytes(plans, steps), dtype=torch.uint8, device="cuda")
+    eb.batch_run(plans, xs, ys, steps, ws)
+    torch.cuda.synchronize()
+    for p, x, y, st in zip(plans, xs, ys, steps):
+        assert torch.equal(y, alone(p, x, st))
