@@ -61,6 +61,10 @@ def _load():
                                            ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_run_varcoef.restype = ctypes.c_int
+        lib.oracle_run_varcoef.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int,
+                                           ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int64]
         lib.oracle_reduce.restype = ctypes.c_int
         lib.oracle_reduce.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.c_int,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
@@ -126,6 +130,26 @@ def run_offsets(grid: np.ndarray, offsets, radius: int, coeffs, boundary: int, s
                                 g.ctypes.data, out.ctypes.data, int(steps), int(nthreads))
     if rc != 0:
         raise ValueError(f"oracle_run_offsets failed ({rc})")
+    return out
+
+
+def run_varcoef(grid: np.ndarray, shape: int, radius: int, field: np.ndarray, boundary: int,
+                steps: int) -> np.ndarray:
+    """Jacobi steps with per-cell weights: `field` has shape (npts,) +
+    grid.shape, entry [k][x] the weight of offset k (canonical order) at
+    cell x (pad entries unused).  Single-threaded plain loops."""
+    lib = _load()
+    g = np.ascontiguousarray(grid, dtype=np.float64)
+    f = np.ascontiguousarray(field, dtype=np.float64)
+    if f.shape != (npoints(g.ndim, shape, radius),) + g.shape:
+        raise ValueError("field must hold one array per offset, shaped like the grid")
+    pad = radius if boundary == DIRICHLET else 0
+    dims = (ctypes.c_int64 * g.ndim)(*[s - 2 * pad for s in g.shape])
+    out = np.empty_like(g)
+    rc = lib.oracle_run_varcoef(g.ndim, dims, shape, radius, f.ctypes.data, boundary, g.ctypes.data,
+                                out.ctypes.data, int(steps))
+    if rc != 0:
+        raise ValueError(f"oracle_run_varcoef failed ({rc})")
     return out
 
 

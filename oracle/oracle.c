@@ -209,6 +209,77 @@ int oracle_run(int ndim, const int64_t* dims, int shape, int radius,
     return rc;
 }
 
+/* Variable coefficients (an extension; the paper's stencils have fixed
+ * weights): u_s(x) = sum_k c_k(x) * u_{s-1}(x + o_k), the weights of cell x
+ * read from `field`, which holds npts arrays laid out like the stored grid
+ * (array k starts at field + k * stored elements; pad entries unused).
+ * Offsets of a named shape, canonical order; other arguments as for
+ * oracle_run. */
+int oracle_run_varcoef(int ndim, const int64_t* dims, int shape, int radius,
+                       const double* field, int boundary, const double* in,
+                       double* out, int64_t steps)
+{
+    int npts = oracle_offsets(ndim, shape, radius, NULL, NULL, NULL);
+    if (npts < 0 || steps < 0 || !dims || !field || !in || !out || in == out)
+        return -1;
+    if (boundary != OR_DIRICHLET && boundary != OR_PERIODIC)
+        return -1;
+    int64_t n[3] = {1, 1, 1};
+    for (int d = 0; d < ndim; d++) {
+        if (dims[d] < 1) return -1;
+        n[3 - ndim + d] = dims[d];
+    }
+    int pad = (boundary == OR_DIRICHLET) ? radius : 0;
+    int zpad = (ndim == 3) ? pad : 0;
+    int64_t ext[3];
+    for (int d = 0; d < 3; d++)
+        ext[d] = n[d] + ((d >= 3 - ndim) ? 2 * pad : 0);
+    int64_t total = ext[0] * ext[1] * ext[2];
+    int64_t sy = ext[2], sz = ext[1] * ext[2];
+    int* oz = malloc(sizeof(int) * npts);
+    int* oy = malloc(sizeof(int) * npts);
+    int* ox = malloc(sizeof(int) * npts);
+    double* tmp = malloc(sizeof(double) * (size_t)total);
+    if (!oz || !oy || !ox || !tmp) {
+        free(oz); free(oy); free(ox); free(tmp);
+        return -2;
+    }
+    oracle_offsets(ndim, shape, radius, oz, oy, ox);
+    memcpy(out, in, sizeof(double) * (size_t)total);
+    memcpy(tmp, in, sizeof(double) * (size_t)total);
+    double* a = (steps % 2 == 0) ? out : tmp;
+    double* b = (steps % 2 == 0) ? tmp : out;
+    for (int64_t s = 0; s < steps; s++) {
+        for (int64_t z = 0; z < n[0]; z++)
+            for (int64_t y = 0; y < n[1]; y++)
+                for (int64_t x = 0; x < n[2]; x++) {
+                    int64_t zo = (boundary == OR_PERIODIC) ? z : z + zpad;
+                    int64_t yo = (boundary == OR_PERIODIC) ? y : y + pad;
+                    int64_t xo = (boundary == OR_PERIODIC) ? x : x + pad;
+                    int64_t self = zo * sz + yo * sy + xo;
+                    double acc = 0.0;
+                    for (int k = 0; k < npts; k++) {
+                        int64_t zz, yy, xx;
+                        if (boundary == OR_PERIODIC) {
+                            zz = wrap(z + oz[k], n[0]);
+                            yy = wrap(y + oy[k], n[1]);
+                            xx = wrap(x + ox[k], n[2]);
+                        } else {
+                            zz = z + oz[k] + zpad;
+                            yy = y + oy[k] + pad;
+                            xx = x + ox[k] + pad;
+                        }
+                        double term = field[(int64_t)k * total + self] * a[zz * sz + yy * sy + xx];
+                        acc = acc + term;
+                    }
+                    b[self] = acc;
+                }
+        double* t = a; a = b; b = t;
+    }
+    free(oz); free(oy); free(ox); free(tmp);
+    return 0;
+}
+
 /* Interior reductions used for verification and reporting (FP64):
  *   res[0] = sum of interior values (Neumaier compensated summation),
  *   res[1] = sqrt(sum of squares)   (compensated),

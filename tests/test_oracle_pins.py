@@ -162,6 +162,59 @@ def test_offset_list_bruteforce(ndim, boundary):
         np.testing.assert_allclose(out, ref, rtol=1e-14, atol=1e-14)
 
 
+def dense_operator_varcoef(stored_shape, offs, field, r, boundary):
+    """Matrix M with u_s = M u_{s-1}: row i holds cell i's own weights."""
+    shp = stored_shape
+    ndim = len(shp)
+    N = int(np.prod(shp))
+    M = np.zeros((N, N))
+    pad = r if boundary == synth.DIRICHLET else 0
+    for idx in itertools.product(*[range(s) for s in shp]):
+        i = np.ravel_multi_index(idx, shp)
+        if not all(pad <= v < s - pad for v, s in zip(idx, shp)):
+            M[i, i] = 1.0
+            continue
+        for k, (dz, dy, dx) in enumerate(offs):
+            d = (dy, dx) if ndim == 2 else (dz, dy, dx)
+            nb = tuple(v + o for v, o in zip(idx, d))
+            if boundary == synth.PERIODIC:
+                nb = tuple(v % s for v, s in zip(nb, shp))
+            M[i, np.ravel_multi_index(nb, shp)] += field[k][idx]
+    return M
+
+
+@pytest.mark.parametrize("boundary", [synth.DIRICHLET, synth.PERIODIC])
+@pytest.mark.parametrize("ndim,shape,r", [(2, synth.STAR, 1), (2, synth.BOX, 2), (3, synth.STAR, 1)])
+def test_varcoef_bruteforce(ndim, shape, r, boundary):
+    rng = np.random.default_rng(30 + ndim + r)
+    dims = (8, 7) if ndim == 2 else (5, 4, 6)
+    g = synth.grid(dims, r, boundary, seed=31)
+    offs = independent_offsets(ndim, shape, r)
+    field = rng.random((len(offs),) + g.shape)
+    M = dense_operator_varcoef(g.shape, offs, field, r, boundary)
+    for T in (1, 3):
+        out = oracle.run_varcoef(g, shape, r, field, boundary, T)
+        ref = (np.linalg.matrix_power(M, T) @ g.ravel()).reshape(g.shape)
+        np.testing.assert_allclose(out, ref, rtol=1e-14, atol=1e-14)
+
+
+def test_varcoef_with_uniform_weights_is_the_fixed_stencil():
+    g, c = synth.problem(2, (20, 17), synth.BOX, 1, synth.DIRICHLET, seed=32)
+    field = np.broadcast_to(c[:, None, None], (len(c),) + g.shape).copy()
+    np.testing.assert_array_equal(oracle.run_varcoef(g, synth.BOX, 1, field, synth.DIRICHLET, 5),
+                                  oracle.run(g, synth.BOX, 1, c, synth.DIRICHLET, 5, nthreads=1))
+
+
+def test_varcoef_rows_summing_to_one_keep_a_constant_field():
+    rng = np.random.default_rng(33)
+    dims = (9, 8, 7)
+    w = rng.random((13,) + synth.stored_shape(dims, 2, synth.DIRICHLET))
+    w /= w.sum(axis=0, keepdims=True)
+    g = np.full(synth.stored_shape(dims, 2, synth.DIRICHLET), 0.625)
+    out = oracle.run_varcoef(g, synth.STAR, 2, w, synth.DIRICHLET, 6)
+    assert np.max(np.abs(out - 0.625)) <= 6 * 13 * EPS
+
+
 def test_listing1_1d_special_case():
     # A 2D 5-point star with zero north/south weights is one independent
     # 1D 3-point stencil per row (Listing 1), with fixed end cells.
