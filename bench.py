@@ -361,14 +361,16 @@ def run_ablation(args):
     +LST, +RST; ebisu_plan_set_ablation), then the register-streaming build
     (every level in registers, no barrier; beyond the paper), next to the
     one-step kernel.  Fixed tiles (2D: 1024 columns x 108 rows; 3D: 64 x 32
-    columns x 103 planes), depth t = 4 (2D) / 3 (3D) from +CMQ on."""
+    columns x 103 planes), depth t = 4 (2D) / 3 (3D FP32) / 2 (3D FP64) from
+    +CMQ on."""
     import torch
     from paper_2305_07390_gb300 import ebisu, synth
     stream = torch.cuda.current_stream()
     sh = ebisu.current_stream_handle()
     rows = []
-    cases = [("j2d5pt", 2, (8192, 8192), 96, dict(tile_x=1024, tile_s=108), 4),
-             ("j3d7pt", 3, (512, 512, 512), 24, dict(tile_x=64, tile_y=32, tile_s=103), 3)]
+    # (the 3D FP64 rings at depth 3 exceed shared memory with these tiles: depth 2)
+    cases = [("j2d5pt", 2, (8192, 8192), 96, dict(tile_x=1024, tile_s=108), {"f32": 4, "f64": 4}),
+             ("j3d7pt", 3, (512, 512, 512), 24, dict(tile_x=64, tile_y=32, tile_s=103), {"f32": 3, "f64": 2})]
     for name, nd, dims, steps, tb, tdeep in cases:
         g, c = synth.problem(nd, dims, 0, 1, synth.DIRICHLET, seed=synth.DEFAULT_SEED)
         cells = 1
@@ -394,11 +396,16 @@ def run_ablation(args):
                          "cell_updates_per_s": timed(naive=True)})
             print(json.dumps(rows[-1]), flush=True)
             for label, mask, deep in ABLATION_STEPS:
+                depth = tdeep[dname] if deep else 1
                 plan.set_ablation(0)
-                plan.set_params(**dict(tb, depth=tdeep if deep else 1, ctas_per_sm=2, variant=0))
+                try:
+                    plan.set_params(**dict(tb, depth=depth, ctas_per_sm=2, variant=0))
+                except ebisu.EbisuError as err:
+                    rows.append({"stencil": name, "dtype": dname, "step": label, "refused": str(err)})
+                    continue
                 plan.set_ablation(mask)
                 rows.append({"stencil": name, "dtype": dname, "step": label, "mask": mask,
-                             "depth": tdeep if deep else 1, "cell_updates_per_s": timed()})
+                             "depth": depth, "cell_updates_per_s": timed()})
                 print(json.dumps(rows[-1]), flush=True)
             plan.set_ablation(0)
             lo, hi = plan.rs_depths()

@@ -230,6 +230,21 @@ enum ebisu_ablate {
 };
 int ebisu_plan_set_ablation(ebisu_plan_t plan, int mask);
 
+/* Variable coefficients (an extension; the paper's weights are fixed):
+ * with a field set, every step computes
+ *     u_s(x) = sum_k c_k(x) * u_{s-1}(x + o_k)
+ * in canonical offset order (acc = c_0(x) u(o_0), then FMAs), the weights of
+ * cell x read from `field`: a DEVICE array of P arrays laid out like the
+ * stored grid (array k starts at field + k * ebisu_plan_grid_elems; the
+ * entries of pad cells are unused), in the accumulation type (double for
+ * EBISU_F64, float for EBISU_F32 and EBISU_BF16), owned by the caller and
+ * read during every run.  Every step reads P weights per cell, which no
+ * temporal blocking can spare, so such plans run the one-step kernel
+ * whatever their parameters; tuning, batches and the server refuse them
+ * (EBISU_ERR_UNSUPPORTED), as do stochastic rounding and ablation.
+ * field = NULL restores the plan's fixed coefficients.  Host only. */
+int ebisu_plan_set_coefficient_field(ebisu_plan_t plan, const void* field);
+
 /* Temporal depths built for the register-streaming kernel (variant 2) of
  * this plan's stencil and storage type (Section 4's temporal blocking with
  * the per-level queues held in registers): *shallow <= *deep.  3D plans: 1

@@ -111,8 +111,10 @@ int layout(ebisu_batch_s* b)
         // (a plan whose tuner preferred the one-step kernel keeps the best
         // fused parameters too)
         const bool rs = uses_rs(&b->plans[i]);
-        // stochastic rounding exists in the register-streaming build only
+        // stochastic rounding exists in the register-streaming build only;
+        // per-cell weights in the one-step kernel only
         if (!rs && plan_sr(&b->plans[i]) && b->steps[i] > 0) return EBISU_ERR_UNSUPPORTED;
+        if (b->plans[i].field && b->steps[i] > 0) return EBISU_ERR_UNSUPPORTED;
         if (rs) {
             b->plans[i].prm.variant = 2;
         } else {

@@ -35,6 +35,8 @@ struct PadParams {
                                     const NaiveParams& p, cudaStream_t st);                      \
     cudaError_t pad_copy_##NAME(const void* s, void* d0, void* d1, const PadParams& p,           \
                                 cudaStream_t st);                                                \
+    cudaError_t naive_vc_launch_##NAME(int d, int s, int r, const void* a, void* b, const void* f, \
+                                       int64_t fs, const NaiveParams& p, cudaStream_t st);       \
     cudaError_t reduce_partial_##NAME(const void* a, const void* b, double* part,                \
                                       const PadParams& p, int64_t* n, cudaStream_t st);
 

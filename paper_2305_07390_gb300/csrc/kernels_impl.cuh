@@ -77,6 +77,60 @@ __global__ void __launch_bounds__(256) naive_kernel(const T* __restrict__ src, T
 }
 
 // ---------------------------------------------------------------------------
+// Variable coefficients: the same one-step sweep with the weights of cell x
+// read from `field` (P arrays laid out like the stored grid, array k at
+// field + k * fstride, in the accumulation type).  Each step reads P weights
+// per cell, which no temporal blocking can spare (they are not produced by
+// the previous step), so plans with a coefficient field run this kernel.
+
+template <class T, int DIM, int SHAPE, int R>
+__global__ void __launch_bounds__(256) naive_vc_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                                                       const typename DT<T>::C* __restrict__ field,
+                                                       int64_t fstride, const __grid_constant__ NaiveParams a)
+{
+    using St = Stencil<DIM, SHAPE, R>;
+    using D = DT<T>;
+    using C = typename D::C;
+    constexpr int P = St::P;
+    constexpr auto OFF = St::kOff;
+    const int64_t n0 = a.n[0];
+    const int n1 = (int)a.n[1], n2 = (int)a.n[2];
+    const int q2 = blockIdx.x * 32 + threadIdx.x;
+    const int q1 = (DIM == 3) ? (int)(blockIdx.y * 8 + threadIdx.y) : 0;
+    if (q2 >= n2 || q1 >= n1) return;
+    const int pad = a.pad, pad1 = (DIM == 3) ? a.pad : 0;
+    const int64_t lds = a.lds, ld1 = a.ld1;
+#pragma unroll
+    for (int i = 0; i < kNaiveRows; ++i) {
+        const int64_t ps = (DIM == 3) ? (int64_t)blockIdx.z * kNaiveRows + i
+                                      : ((int64_t)blockIdx.y * kNaiveRows + i) * 8 + threadIdx.y;
+        if (ps >= n0) return;
+        int64_t o;
+        C acc;
+        if (a.periodic) {
+            o = ps * lds + (int64_t)q1 * ld1 + q2;
+            auto at = [&](int k) -> C {
+                const int64_t s_ = wrap_idx(ps + OFF.ds[k], n0);
+                const int64_t y_ = (DIM == 3) ? wrap_idx(q1 + OFF.d1[k], n1) : 0;
+                const int64_t x_ = wrap_idx(q2 + OFF.d2[k], n2);
+                return D::load_ro(src + s_ * lds + y_ * ld1 + x_);
+            };
+            acc = D::mul(__ldg(field + o), at(0));
+#pragma unroll
+            for (int k = 1; k < P; ++k) acc = D::fma(__ldg(field + k * fstride + o), at(k), acc);
+        } else {
+            o = (ps + pad) * lds + (int64_t)(q1 + pad1) * ld1 + (q2 + pad);
+            const T* p = src + o;
+            auto at = [&](int k) -> C { return D::load_ro(p + OFF.ds[k] * lds + OFF.d1[k] * ld1 + OFF.d2[k]); };
+            acc = D::mul(__ldg(field + o), at(0));
+#pragma unroll
+            for (int k = 1; k < P; ++k) acc = D::fma(__ldg(field + k * fstride + o), at(k), acc);
+        }
+        dst[o] = D::narrow(acc);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Copy the Dirichlet pad of `src` into up to two destinations.  Pad cells are
 // enumerated directly: the 2*pad pad planes along s, the pad rows of interior
 // planes, then the pad cells of interior rows (stored coordinates).
@@ -284,6 +338,28 @@ static cudaError_t naive_launch_t(int dim, int shape, int r, const void* src, vo
 }
 
 template <class T>
+static cudaError_t naive_vc_launch_t(int dim, int shape, int r, const void* src, void* dst, const void* field,
+                                     int64_t fstride, const NaiveParams& p, cudaStream_t st)
+{
+    const void* k = nullptr;
+#define X(D_, S_, R_) \
+    if (dim == D_ && shape == S_ && r == R_) k = (const void*)&naive_vc_kernel<T, D_, S_, R_>;
+    EBISU_FOR_EACH_STENCIL(X)
+#undef X
+    if (!k) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((p.n[2] + 31) / 32), 1, 1);
+    if (dim == 3) {
+        grid.y = (unsigned)((p.n[1] + 7) / 8);
+        grid.z = (unsigned)((p.n[0] + kNaiveRows - 1) / kNaiveRows);
+    } else {
+        grid.y = (unsigned)((p.n[0] + 8 * kNaiveRows - 1) / (8 * kNaiveRows));
+    }
+    if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+    void* args[] = {(void*)&src, (void*)&dst, (void*)&field, (void*)&fstride, (void*)&p};
+    return cudaLaunchKernel(k, grid, dim3(32, 8), args, 0, st);
+}
+
+template <class T>
 static cudaError_t pad_copy_t(const void* src, void* d0, void* d1, const PadParams& p, cudaStream_t st)
 {
     const int64_t E1 = p.n[1] + 2 * p.pad1, E2 = p.n[2] + 2 * p.pad;
@@ -330,6 +406,11 @@ static cudaError_t reduce_partial_t(const void* a, const void* b, double* part, 
                                 cudaStream_t st)                                                 \
     {                                                                                            \
         return pad_copy_t<T>(s, d0, d1, p, st);                                                  \
+    }                                                                                            \
+    cudaError_t naive_vc_launch_##NAME(int d, int s, int r, const void* a, void* b, const void* f, \
+                                       int64_t fs, const NaiveParams& p, cudaStream_t st)        \
+    {                                                                                            \
+        return naive_vc_launch_t<T>(d, s, r, a, b, f, fs, p, st);                                \
     }                                                                                            \
     cudaError_t reduce_partial_##NAME(const void* a, const void* b, double* part,                \
                                       const PadParams& p, int64_t* n, cudaStream_t st)           \

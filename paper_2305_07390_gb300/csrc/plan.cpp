@@ -274,6 +274,16 @@ static NaiveParams naive_params(const ebisu_plan_s* p)
     return a;
 }
 
+cudaError_t naive_vc_launch(const ebisu_plan_s* p, const void* src, void* dst, cudaStream_t st)
+{
+    const NaiveParams a = naive_params(p);
+    switch (p->dtype) {
+    case EBISU_F64: return naive_vc_launch_f64(p->ndim, p->shape, p->radius, src, dst, p->field, p->elems, a, st);
+    case EBISU_F32: return naive_vc_launch_f32(p->ndim, p->shape, p->radius, src, dst, p->field, p->elems, a, st);
+    default: return naive_vc_launch_bf16(p->ndim, p->shape, p->radius, src, dst, p->field, p->elems, a, st);
+    }
+}
+
 cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, int64_t t, cudaStream_t st)
 {
     NaiveParams a = naive_params(p);
@@ -750,7 +760,7 @@ int ebisu_plan_set_rounding(ebisu_plan_t plan, int rounding, uint64_t seed)
 {
     if (!plan) return EBISU_ERR_INVALID_ARG;
     if (rounding != EBISU_ROUND_NEAREST && rounding != EBISU_ROUND_STOCHASTIC) return EBISU_ERR_INVALID_ARG;
-    if (rounding == EBISU_ROUND_STOCHASTIC && plan->dtype != EBISU_BF16) return EBISU_ERR_UNSUPPORTED;
+    if (rounding == EBISU_ROUND_STOCHASTIC && (plan->dtype != EBISU_BF16 || plan->field)) return EBISU_ERR_UNSUPPORTED;
     plan->rounding = rounding;
     plan->sr_seed = seed;
     plan->sr_key = sr_plan_key(seed);
@@ -803,6 +813,16 @@ int ebisu_plan_set_ablation(ebisu_plan_t plan, int mask)
     return EBISU_OK;
 }
 
+int ebisu_plan_set_coefficient_field(ebisu_plan_t plan, const void* field)
+{
+    if (!plan) return EBISU_ERR_INVALID_ARG;
+    if (field && (plan_sr(plan) || plan->ablate)) return EBISU_ERR_UNSUPPORTED;
+    const size_t align = plan->dtype == EBISU_F64 ? 8 : 4;
+    if (((uintptr_t)field) % align != 0) return EBISU_ERR_INVALID_ARG;
+    plan->field = field;
+    return EBISU_OK;
+}
+
 int ebisu_plan_get_rounding(ebisu_plan_t plan, int* rounding, uint64_t* seed)
 {
     if (!plan || !rounding) return EBISU_ERR_INVALID_ARG;
@@ -851,8 +871,8 @@ static int run_common(ebisu_plan_t p, const void* in, void* out, int64_t steps, 
         }
         return EBISU_OK;
     }
-    if (!naive && p->prm.variant == 2) return run_rs(p, in, out, steps, ws, st, debug_stall);
-    if (naive || p->prm.variant == 1) {
+    if (!naive && !p->field && p->prm.variant == 2) return run_rs(p, in, out, steps, ws, st, debug_stall);
+    if (naive || p->prm.variant == 1 || p->field) {
         // one launch per step; buffers alternate so that the last lands in out
         const void* src = in;
         if (in == out && (steps % 2 == 1)) {
@@ -868,7 +888,7 @@ static int run_common(ebisu_plan_t p, const void* in, void* out, int64_t steps, 
         if (e != cudaSuccess) return fail_cuda(e);
         for (int64_t s = 0; s < steps; ++s) {
             void* dst = ((steps - 1 - s) % 2 == 0) ? out : wsgrid;
-            e = naive_launch(p, src, dst, s + 1, st);
+            e = p->field ? naive_vc_launch(p, src, dst, st) : naive_launch(p, src, dst, s + 1, st);
             if (e != cudaSuccess) return fail_cuda(e);
             src = dst;
         }

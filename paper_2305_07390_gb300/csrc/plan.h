@@ -29,6 +29,7 @@ struct ebisu_plan_s {
     uint64_t sr_seed = 0;
     uint32_t sr_key = 0;
     int ablate = 0;  // shared-memory build with elements switched off (EBISU_ABLATE_* mask)
+    const void* field = nullptr;  // per-cell weights (device; P arrays like the grid), or null
 };
 
 namespace ebisu {
@@ -95,6 +96,8 @@ cudaError_t tb_occupancy(const ebisu_plan_s* p, int variant, size_t smem, int* b
 // one step (t = 1 .. steps: the step whose result is written; stochastic
 // rounding keys its random bits on it)
 cudaError_t naive_launch(const ebisu_plan_s* p, const void* src, void* dst, int64_t t, cudaStream_t st);
+// one step with the plan's per-cell weights (variable coefficients)
+cudaError_t naive_vc_launch(const ebisu_plan_s* p, const void* src, void* dst, cudaStream_t st);
 // does the plan store BF16 with stochastic rounding (its own kernel builds)?
 inline bool plan_sr(const ebisu_plan_s* p) { return p->dtype == EBISU_BF16 && p->rounding == EBISU_ROUND_STOCHASTIC; }
 cudaError_t pad_copy(const ebisu_plan_s* p, const void* src, void* d0, void* d1, cudaStream_t st);

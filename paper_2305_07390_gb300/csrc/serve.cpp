@@ -353,6 +353,7 @@ int ebisu_serve_submit(ebisu_server_t s, ebisu_plan_t plan, const void* in_dev, 
                        uint64_t* ticket)
 {
     if (!s || !plan || !in_dev || !out_dev || !ticket || steps < 0) return EBISU_ERR_INVALID_ARG;
+    if (plan->field) return EBISU_ERR_UNSUPPORTED;  // the server runs batches, which take fixed weights
     Request* r = new (std::nothrow) Request();
     if (!r) return EBISU_ERR_OOM;
     r->plan = *plan;

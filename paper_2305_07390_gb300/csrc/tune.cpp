@@ -318,6 +318,7 @@ int ebisu_plan_tune_share(ebisu_plan_t plan, const void* in, void* out, int64_t 
 {
     if (!plan || !in || !out || !workspace || steps < 1 || max_candidates < 1) return EBISU_ERR_INVALID_ARG;
     if (!(share > 0.0 && share <= 1.0)) return EBISU_ERR_INVALID_ARG;
+    if (plan->field) return EBISU_ERR_UNSUPPORTED;  // one kernel only: nothing to choose
     if (in == out) return EBISU_ERR_INVALID_ARG;
     std::vector<ebisu_params> cand(max_candidates);
     std::vector<double> pred(max_candidates);

@@ -84,6 +84,7 @@ SIGNATURES = {
     "ebisu_plan_rs_depths": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "ebisu_plan_set_rounding": (_I, [_P, _I, ctypes.c_uint64]),
     "ebisu_plan_set_ablation": (_I, [_P, _I]),
+    "ebisu_plan_set_coefficient_field": (_I, [_P, _P]),
     "ebisu_plan_get_rounding": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_uint64)]),
     "ebisu_plan_workspace_bytes": (_I, [_P, ctypes.POINTER(_SZ)]),
     "ebisu_run": (_I, [_P, _P, _P, _I64, _P, _P]),
@@ -297,6 +298,21 @@ class Plan:
         """Storage rounding: ROUND_NEAREST or (BF16 only) ROUND_STOCHASTIC."""
         _check(lib().ebisu_plan_set_rounding(self.h, int(rounding), ctypes.c_uint64(int(seed))),
                "ebisu_plan_set_rounding")
+
+    def set_coefficient_field(self, field):
+        """Per-cell weights: a CUDA tensor of shape (P,) + stored shape in the
+        accumulation type (float64 for F64, float32 for F32/BF16), or None."""
+        if field is None:
+            self._field = None
+            _check(lib().ebisu_plan_set_coefficient_field(self.h, None), "ebisu_plan_set_coefficient_field")
+            return
+        torch = _torch()
+        want = torch.float64 if self.dtype == F64 else torch.float32
+        assert field.is_cuda and field.dtype == want and field.is_contiguous()
+        assert tuple(field.shape[1:]) == self.stored_shape
+        self._field = field  # keep it alive while the plan may read it
+        _check(lib().ebisu_plan_set_coefficient_field(self.h, ctypes.c_void_p(field.data_ptr())),
+               "ebisu_plan_set_coefficient_field")
 
     def set_ablation(self, mask):
         """Switch elements of the shared-memory build off (EBISU_ABLATE_* mask)."""
