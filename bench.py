@@ -492,7 +492,7 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
             if key not in tuned:
                 # the grid's share of the GPU inside the batch: its cells over the total
                 ws = plan.workspace()
-                plan.tune(x, y, 32, ws, max_candidates=6, share=min(1.0, ny * nx / cells))
+                plan.tune(x, y, 96, ws, max_candidates=6, share=min(1.0, ny * nx / cells))
                 tuned[key] = plan.params()
                 del ws
             elif not apply_params(ebisu, plan, tuned[key]):
@@ -921,7 +921,9 @@ def main():
             xl = p["x"].to(ebisu.torch_dtype(dt))
             yl = torch.empty_like(xl)
             wsl = plan.workspace()
-            plan.tune(xl, yl, min(steps, 48), wsl, max_candidates=args.tune)
+            # (the register-streaming choices differ by a few percent: time
+            # enough temporal blocks that the pipeline ramp does not decide)
+            plan.tune(xl, yl, min(steps, 192), wsl, max_candidates=args.tune)
             q = plan.params()
             tuned = q.variant
             if q.variant == 1:

@@ -419,6 +419,9 @@ int ebisu_reduce(ebisu_plan_t plan, const void* a, const void* b,
  *                           pointers; in[i] == out[i] is allowed).
  *   workspace             : device memory of ebisu_batch_workspace_bytes
  *                           bytes, 256-byte aligned.
+ * Groups launch concurrently: each on a stream of the batch's own, forked
+ * from `stream` and joined back into it by events (so the whole launch stays
+ * one unit on `stream`, and stays capturable into a CUDA graph).
  * ebisu_batch_run = create + launch + destroy.  To replay a batch cheaply,
  * ebisu_batch_create uploads the work tables into the workspace once
  * (synchronising the stream); ebisu_batch_launch then enqueues only stream

@@ -58,6 +58,19 @@ struct ebisu_batch_s {
     size_t desc_off = 0, rsdesc_off = 0, total = 0;
     void* ws = nullptr;
     bool uploaded = false;
+    // several kernel groups run concurrently: each on a stream of its own,
+    // forked from and joined back into the caller's stream by events
+    std::vector<cudaStream_t> gstreams;
+    std::vector<cudaEvent_t> gdone;
+    cudaEvent_t fork = nullptr;
+    ~ebisu_batch_s()
+    {
+        // (destruction with work in flight is allowed: the runtime releases
+        // streams and events once their work completes)
+        for (cudaStream_t s : gstreams) cudaStreamDestroy(s);
+        for (cudaEvent_t e : gdone) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+    }
 };
 
 namespace {
@@ -309,6 +322,23 @@ int ebisu_batch_create(int n, const ebisu_plan_t* plans, const void* const* in, 
     }
     b->items.clear();
     b->items.shrink_to_fit();
+    int launched = 0;
+    for (const BatchGroup& g : b->groups) launched += (g.nitems > 0) ? 1 : 0;
+    if (launched > 1) {
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
+            cudaStream_t gs = nullptr;
+            cudaEvent_t ge = nullptr;
+            e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) b->gstreams.push_back(gs);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ge, cudaEventDisableTiming);
+            if (e == cudaSuccess) b->gdone.push_back(ge);
+        }
+        if (e != cudaSuccess) {
+            delete b;
+            return fail_cuda(e);
+        }
+    }
     b->uploaded = true;
     *res = b;
     return EBISU_OK;
@@ -332,9 +362,17 @@ int ebisu_batch_launch(ebisu_batch_t b, void* stream)
             e = cudaMemcpyAsync(ws + b->grid_off[i], b->in[i], bytes, cudaMemcpyDeviceToDevice, st);
         }
     }
+    const bool forked = !b->gstreams.empty();
+    if (forked && e == cudaSuccess) e = cudaEventRecord(b->fork, st);
     for (size_t gi = 0; gi < b->groups.size() && e == cudaSuccess; ++gi) {
         const BatchGroup& g = b->groups[gi];
         if (g.nitems == 0) continue;
+        cudaStream_t gst = st;
+        if (forked) {
+            gst = b->gstreams[gi];
+            e = cudaStreamWaitEvent(gst, b->fork, 0);
+            if (e != cudaSuccess) break;
+        }
         if (g.rs) {
             RSParams prm;
             memset(&prm, 0, sizeof(prm));
@@ -343,18 +381,22 @@ int ebisu_batch_launch(ebisu_batch_t b, void* stream)
             prm.nitems = g.nitems;
             prm.ctl = (Control*)(ws + g.ctl_off);
             prm.timeout_ns = wait_timeout_ns();
-            e = rs_launch(g.kind, g.variant, prm, g.grid, st);
-            continue;
+            e = rs_launch(g.kind, g.variant, prm, g.grid, gst);
+        } else {
+            TBParams prm;
+            memset(&prm, 0, sizeof(prm));
+            prm.grids = (const GridDesc*)(ws + b->desc_off);
+            prm.items = (const int32_t*)(ws + g.items_off);
+            prm.nitems = g.nitems;
+            prm.ctl = (Control*)(ws + g.ctl_off);
+            prm.timeout_ns = wait_timeout_ns();
+            prm.smem_plane = g.plane_cap;
+            e = tb_launch(g.kind, g.variant, prm, g.grid, g.smem, gst);
         }
-        TBParams prm;
-        memset(&prm, 0, sizeof(prm));
-        prm.grids = (const GridDesc*)(ws + b->desc_off);
-        prm.items = (const int32_t*)(ws + g.items_off);
-        prm.nitems = g.nitems;
-        prm.ctl = (Control*)(ws + g.ctl_off);
-        prm.timeout_ns = wait_timeout_ns();
-        prm.smem_plane = g.plane_cap;
-        e = tb_launch(g.kind, g.variant, prm, g.grid, g.smem, st);
+        if (forked && e == cudaSuccess) {
+            e = cudaEventRecord(b->gdone[gi], gst);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->gdone[gi], 0);
+        }
     }
     if (e != cudaSuccess) return fail_cuda(e);
     return EBISU_OK;

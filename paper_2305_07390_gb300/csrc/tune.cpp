@@ -350,7 +350,7 @@ int ebisu_plan_tune_share(ebisu_plan_t plan, const void* in, void* out, int64_t 
             const int64_t S = rs3_strip(es, D, plan->radius), TY = rs3_rows(es);
             const int64_t xy = ((plan->n[2] + S - 1) / S) * ((plan->n[1] + TY - 1) / TY);
             int64_t lastH = -1;
-            for (int k : {1, 2, 4}) {
+            for (int k : {1, 2, 3, 4, 6}) {
                 const int64_t ng = std::max<int64_t>(1, (k * warps + xy - 1) / xy);
                 const int64_t H = (plan->n[0] + ng - 1) / ng;
                 if (H == lastH) continue;
@@ -387,7 +387,7 @@ int ebisu_plan_tune_share(ebisu_plan_t plan, const void* in, void* out, int64_t 
             const int64_t S = kRSCols - 2LL * D * plan->radius;
             const int64_t ns = (plan->n[2] + S - 1) / S;
             int64_t lastH = -1;
-            for (int k : {1, 2, 4}) {
+            for (int k : {1, 2, 3, 4, 6}) {
                 const int64_t ng = std::max<int64_t>(1, (k * warps + ns - 1) / ns);
                 const int64_t H = (plan->n[0] + ng - 1) / ng;
                 if (H == lastH) continue;
