@@ -228,8 +228,23 @@ def run_case(args):
     plan.run(x, y, args.solve_steps, ws, naive=args.naive)
     rc = plan.sync(ws)
     assert rc == 0, ebisu.status_string(rc)
-    print(json.dumps({"case": args.case, "n": args.n, "dtype": args.dtype, "steps": args.solve_steps,
-                      "params": plan.params().as_dict(), "naive": args.naive}))
+    out = {"case": args.case, "n": args.n, "dtype": args.dtype, "steps": args.solve_steps,
+           "params": plan.params().as_dict(), "naive": args.naive}
+    if args.repeat > 0:
+        # the same solve again, timed with CUDA events on the launching stream
+        stream = torch.cuda.current_stream()
+        sh = ebisu.current_stream_handle()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.repeat):
+            plan.run(x, y, args.solve_steps, ws, stream=sh, naive=args.naive)
+        b.record(stream)
+        b.synchronize()
+        rc = plan.sync(ws)
+        assert rc == 0, ebisu.status_string(rc)
+        ms = a.elapsed_time(b) / args.repeat
+        out.update(ms=ms, cell_updates_per_s=args.n ** nd * args.solve_steps / (ms * 1e-3))
+    print(json.dumps(out))
 
 
 def run_set3d(args):
@@ -720,6 +735,7 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"], help="--case: storage type")
     ap.add_argument("--params", default="", help="--case: plan parameters, k=v,k=v")
     ap.add_argument("--naive", action="store_true", help="--case: the one-step-per-launch kernel")
+    ap.add_argument("--repeat", type=int, default=0, help="--case: time this many further solves")
     ap.add_argument("--ablate", type=int, default=0, help="--case: ablation mask of the shared-memory build")
     ap.add_argument("--workload", default="set", choices=["set", "set3d", "batch", "serve", "paper", "ablation"],
                     help="set: the FP64 2D stencil set (default, the headline line); set3d: the FP64 3D "

@@ -86,8 +86,8 @@ constexpr int rs_depth(int esize, int shape /*0 star, 1 box*/, int r, int which)
 }
 
 // 3D register-streaming builds: which stencils they cover (FP64 at depth 1:
-// the 7- and 13-point stars and the 27-point box; FP32 and BF16 temporally
-// blocked: radius 1) and the rows of a warp's patch.
+// the 7- and 13-point stars and the radius-1 boxes; FP32 and BF16
+// temporally blocked: radius 1) and the rows of a warp's patch.
 constexpr bool rs3_built(int esize, int shape, int r)
 {
     return (esize == 8 && (r == 1 || (shape == 0 && r == 2))) || (esize != 8 && r == 1);
@@ -96,15 +96,18 @@ constexpr bool rs3_built(int esize, int shape, int r)
 constexpr int rs3_rows(int esize) { return esize == 8 ? 2 : 4; }
 constexpr int kRS3Cols = 64;  // columns a warp holds (32 lanes x 2)
 // output columns per 64-column strip: the patch loses t*r columns per side;
-// the FP32/BF16 build at even depth also shifts the patch one column left so
-// that a lane's column pair starts on an even column
+// the FP32/BF16 build shifts the patch one column left when r(t-1) is odd so
+// that a lane's column pair starts on an even stored column
 constexpr int rs3_strip(int esize, int depth, int r)
 {
-    return kRS3Cols - 2 * depth * r - ((esize != 8 && depth % 2 == 0) ? 2 : 0);
+    return kRS3Cols - 2 * depth * r - ((esize != 8 && ((r * (depth - 1)) & 1)) ? 2 : 0);
 }
-// temporal depths built (FP64: 1; FP32/BF16: 7-point star 2 and 3, 27-point
-// box 2)
-constexpr int rs3_depth(int esize, int shape, int which) { return esize == 8 ? 1 : ((which && shape == 0) ? 3 : 2); }
+// temporal depths built (FP64: 1; FP32/BF16: 7-point star 2 and 3, the
+// other radius-1 stencils 2)
+constexpr int rs3_depth(int esize, int shape, int r, int which)
+{
+    return esize == 8 ? 1 : ((which && shape == 0 && r == 1) ? 3 : 2);
+}
 
 // Depth the register-streaming build defaults to (FP32/BF16 storage): the
 // faster of the two built depths on 8192^2 grids (measured on GB300).
@@ -165,8 +168,10 @@ struct RS3Params {
     int32_t S;           // output columns per strip (64 - 2 * depth * radius)
     int32_t H;           // output planes per z segment
     int32_t nstrips, nbands, nsegs;
-    int32_t nblocks;     // ceil(steps / depth)
-    int32_t depth_last;  // steps done by the last block (<= depth)
+    int32_t nblocks;     // temporal blocks of this launch (each of `depth` steps)
+    int32_t nstages;     // buffer writes of the whole run: the blocks, then one
+                         // per remaining one-step launch; block b writes `out`
+                         // when nstages - 1 - b is even, else `ws`
     int32_t debug_stall;
     uint32_t sr_key;     // stochastic-rounding plan key (BF16-SR storage only)
     int32_t reserved_;

@@ -23,7 +23,9 @@
 //  * Level-0 planes are staged 4 planes ahead in shared memory by per-lane
 //    cp.async (each lane copies and later reads back only its own cells).
 //  * Dirichlet pad cells keep their input value at every level (copied from
-//    the level below); levels past the last block's depth pass values on.
+//    the level below).
+//  * Every launch runs whole temporal blocks of depth t; the host runs the
+//    remaining steps % t steps with the one-step kernel.
 //  * Tiles (strip, band, z segment) of block b wait only for their 3 x 3 x 3
 //    neighbours of block b-1 (a tile's inputs reach t cells past its output,
 //    at most one patch, strip or segment away).
@@ -151,9 +153,7 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
         if (!__all_sync(FULL, ok)) return;
 
         // ---- geometry ----------------------------------------------------------
-        const bool lastb = (blk == prm.nblocks - 1);
-        const int deff = lastb ? prm.depth_last : D;  // levels above deff pass values on
-        const bool dst_is_out = ((prm.nblocks - 1 - blk) & 1) == 0;
+        const bool dst_is_out = ((prm.nstages - 1 - blk) & 1) == 0;
         T* const dst = reinterpret_cast<T*>(dst_is_out ? prm.out : prm.ws);
         const T* const src = (blk == 0) ? reinterpret_cast<const T*>(prm.src0)
                                         : reinterpret_cast<const T*>(dst_is_out ? prm.ws : prm.out);
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
                     const int sp_ = ((u - s - 1) % U + U) % U;  // slot of plane zs - 1
                     const int sn = ((u - s + 1) % U + U) % U;   // slot of plane zs + 1
                     const int ys = ya - (D - s);  // global row of level s's row 0
-                    const bool copy = (s > deff) || (!per && (zs < 0 || zs >= n0));
+                    const bool copy = !per && (zs < 0 || zs >= n0);
                     // x neighbours of level s-1 rows: WL = left lane's last
                     // column, WR = right lane's first column, per plane
                     // (0: zs-1, 1: zs, 2: zs+1) and row
