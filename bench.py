@@ -492,12 +492,17 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
                 refs[(fname, i)] = oracle.run(held, synth.BOX, 1, ch, synth.DIRICHLET, st,
                                               nthreads=os.cpu_count())
     stream = torch.cuda.current_stream()
+    # the grids, generated once for every storage form (same seeds)
+    t0 = time.perf_counter()
+    problems = [synth.problem(2, (ny, nx), synth.BOX, 1, synth.DIRICHLET, seed=synth.DEFAULT_SEED + i)
+                for i, (ny, nx, _) in enumerate(mix)]
+    out["generate_s"] = time.perf_counter() - t0
     for fname, dt, rounding in BATCH_FORMS:
         plans, xs, ys, steps_l = [], [], [], []
         tuned = {}
         t0 = time.perf_counter()
         for i, (ny, nx, st) in enumerate(mix):
-            g, c = synth.problem(2, (ny, nx), synth.BOX, 1, synth.DIRICHLET, seed=synth.DEFAULT_SEED + i)
+            g, c = problems[i]
             plan = ebisu.Plan(2, (ny, nx), ebisu.BOX, 1, c, dt, ebisu.DIRICHLET)
             if rounding == "sr":
                 plan.set_rounding(ebisu.ROUND_STOCHASTIC, synth.DEFAULT_SEED)
@@ -507,7 +512,12 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
             if key not in tuned:
                 # the grid's share of the GPU inside the batch: its cells over the total
                 ws = plan.workspace()
-                plan.tune(x, y, 96, ws, max_candidates=6, share=min(1.0, ny * nx / cells))
+                # FP64 is bound by its FMA pipe at every depth (the tuner keeps
+                # depth 1), so a short run of the top few candidates decides
+                if dt == ebisu.F64:
+                    plan.tune(x, y, 48, ws, max_candidates=4, share=min(1.0, ny * nx / cells))
+                else:
+                    plan.tune(x, y, 64, ws, max_candidates=6, share=min(1.0, ny * nx / cells))
                 tuned[key] = plan.params()
                 del ws
             elif not apply_params(ebisu, plan, tuned[key]):

@@ -94,9 +94,7 @@ enum ebisu_rounding { EBISU_ROUND_NEAREST = 0, EBISU_ROUND_STOCHASTIC = 1 };
  *                    one warp per 64-column patch streamed along z (FP64,
  *                    radius 1 and the 13-point star: 2 rows, depth 1; FP32
  *                    and BF16 radius 1: 4 rows, depth 2 or 3 for the star,
- *                    2 for the box, poisson and j3d17pt; a 3D FP32/BF16 run
- *                    does floor(steps / depth) temporal blocks and then
- *                    steps % depth one-step launches).
+ *                    2 for the box, poisson and j3d17pt).
  *                    depth
  *                    must be one of ebisu_plan_rs_depths(), tile_s is the
  *                    rows (2D) or planes (3D) per segment, ctas_per_sm caps
@@ -336,12 +334,9 @@ const char* ebisu_last_cuda_error(void);
  * measurement decides).  Times up to `max_candidates` parameter sets from the
  * cost model's ranking, plus the naive one-step kernel, on the caller's
  * buffers (in is not modified; out and workspace are overwritten) for `steps`
- * steps each (a 3D register-streaming candidate of depth t: over the
- * largest multiple of t not above `steps`, at least t, its time scaled to
- * `steps`, since its runs end with steps % t one-step launches).  The plan
- * keeps the fastest fused-kernel parameters, with `variant` = 1 if the naive
- * kernel was faster still; `best_ms` (optional) receives the fastest time.
- * Synchronises the stream. */
+ * steps each.  The plan keeps the fastest fused-kernel parameters, with
+ * `variant` = 1 if the naive kernel was faster still; `best_ms` (optional)
+ * receives the fastest time.  Synchronises the stream. */
 int ebisu_plan_tune(ebisu_plan_t plan, const void* in, void* out,
                     int64_t steps, void* workspace, int max_candidates,
                     double* best_ms, void* stream);

@@ -168,10 +168,8 @@ struct RS3Params {
     int32_t S;           // output columns per strip (64 - 2 * depth * radius)
     int32_t H;           // output planes per z segment
     int32_t nstrips, nbands, nsegs;
-    int32_t nblocks;     // temporal blocks of this launch (each of `depth` steps)
-    int32_t nstages;     // buffer writes of the whole run: the blocks, then one
-                         // per remaining one-step launch; block b writes `out`
-                         // when nstages - 1 - b is even, else `ws`
+    int32_t nblocks;     // ceil(steps / depth)
+    int32_t depth_last;  // steps done by the last block (<= depth)
     int32_t debug_stall;
     uint32_t sr_key;     // stochastic-rounding plan key (BF16-SR storage only)
     int32_t reserved_;

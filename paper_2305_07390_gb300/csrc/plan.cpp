@@ -407,11 +407,9 @@ int64_t fill_rs_grid(const ebisu_plan_s* p, const RSLayout& L, const void* in, v
     return nb;
 }
 
-// A run of the 3D register-streaming build (FP64: depth 1; FP32/BF16: depth 2
-// or 3).  The fused launch runs floor(steps / depth) whole temporal blocks;
-// the remaining steps % depth steps follow as one-step launches.  The
-// kernels never write pad cells: the buffers written first get the input's
-// pad from a copy kernel.
+// A run of the 3D register-streaming build (FP64: depth 1; FP32/BF16: depth 2 or
+// 3).  The kernel never writes pad cells: the buffers it writes first get the
+// input's pad from a copy kernel.
 static int run_rs3(ebisu_plan_t p, const void* in, void* out, int64_t steps, void* ws, cudaStream_t st,
                    int debug_stall)
 {
@@ -420,28 +418,23 @@ static int run_rs3(ebisu_plan_t p, const void* in, void* out, int64_t steps, voi
     int rc = rs_layout(p, q, &L);
     if (rc != EBISU_OK) return rc;
     const int D = q.depth;
-    const int64_t nb = steps / D, rem = steps - nb * D;
-    const int64_t nst = nb + rem;  // buffer writes: the blocks, then the one-step launches
+    const int64_t nb = (steps + D - 1) / D;
     const int64_t ntiles = (int64_t)L.nstrips * L.nbands * L.nsegs;
     const DeviceInfo& dv = device_info();
-    if (nb * ntiles + 64LL * 16 * dv.sms * kRSWarps >= (1LL << 32) || nst >= (1LL << 31))
-        return EBISU_ERR_UNSUPPORTED;
+    if (nb * ntiles + 64LL * 16 * dv.sms * kRSWarps >= (1LL << 32)) return EBISU_ERR_UNSUPPORTED;
     const size_t bytes = (size_t)p->elems * p->esize;
     void* wsgrid = (char*)ws + kControlBytes;
     cudaError_t e = cudaSuccess;
-    // stage i writes `out` when nst - 1 - i is even: an in-place run whose
-    // first stage would overwrite its own input reads a copy instead
-    const bool copy_in = (in == out) && (nst % 2 == 1);
+    const bool copy_in = (in == out) && (nb % 2 == 1);
     if (copy_in) {
         e = cudaMemcpyAsync(wsgrid, in, bytes, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return fail_cuda(e);
     }
     const void* src0 = copy_in ? wsgrid : in;
-    auto stage_dst = [&](int64_t i) -> void* { return ((nst - 1 - i) % 2 == 0) ? out : wsgrid; };
     const bool per = p->boundary == EBISU_PERIODIC;
     if (!per) {
-        void* d0 = stage_dst(0);
-        void* d1 = (nst >= 2) ? stage_dst(1) : nullptr;
+        void* d0 = ((nb - 1) % 2 == 0) ? out : wsgrid;
+        void* d1 = (nb >= 2) ? (((nb - 2) % 2 == 0) ? out : wsgrid) : nullptr;
         void* h0 = (d0 != src0 && d0 != in) ? d0 : nullptr;
         void* h1 = (d1 && d1 != src0 && d1 != in) ? d1 : nullptr;
         if (h0 || h1) {
@@ -449,48 +442,40 @@ static int run_rs3(ebisu_plan_t p, const void* in, void* out, int64_t steps, voi
             if (e != cudaSuccess) return fail_cuda(e);
         }
     }
-    if (nb > 0) {
-        RS3Params prm;
-        memset(&prm, 0, sizeof(prm));
-        prm.src0 = src0;
-        prm.out = out;
-        prm.ws = wsgrid;
-        for (int i = 0; i < 3; ++i) prm.n[i] = p->n[i];
-        prm.lds = p->lds;
-        prm.ld1 = p->ld1;
-        prm.nitems = nb * ntiles;
-        prm.ctl = (Control*)ws;
-        prm.timeout_ns = wait_timeout_ns();
-        prm.pad = p->pad;
-        prm.periodic = per ? 1 : 0;
-        prm.S = L.S;
-        prm.H = L.H;
-        prm.nstrips = L.nstrips;
-        prm.nbands = L.nbands;
-        prm.nsegs = L.nsegs;
-        prm.nblocks = (int32_t)nb;
-        prm.nstages = (int32_t)nst;
-        prm.debug_stall = debug_stall;
-        prm.sr_key = p->sr_key;
-        for (int k = 0; k < p->npts; ++k) {
-            prm.coef[k] = p->coef[k];
-            prm.coef_f[k] = (float)p->coef[k];
-        }
-        int occ = 0;
-        e = rs3_occupancy(p, D, &occ);
-        if (e != cudaSuccess) return fail_cuda(e);
-        if (occ < 1) return EBISU_ERR_UNSUPPORTED;
-        int64_t grid = (int64_t)std::min(occ, q.ctas_per_sm) * dv.sms;
-        grid = std::min<int64_t>(grid, (prm.nitems + kRSWarps - 1) / kRSWarps);
-        e = rs3_launch(p, D, prm, (int)grid, st);
-        if (e != cudaSuccess) return fail_cuda(e);
+    RS3Params prm;
+    memset(&prm, 0, sizeof(prm));
+    prm.src0 = src0;
+    prm.out = out;
+    prm.ws = wsgrid;
+    for (int i = 0; i < 3; ++i) prm.n[i] = p->n[i];
+    prm.lds = p->lds;
+    prm.ld1 = p->ld1;
+    prm.nitems = nb * ntiles;
+    prm.ctl = (Control*)ws;
+    prm.timeout_ns = wait_timeout_ns();
+    prm.pad = p->pad;
+    prm.periodic = per ? 1 : 0;
+    prm.S = L.S;
+    prm.H = L.H;
+    prm.nstrips = L.nstrips;
+    prm.nbands = L.nbands;
+    prm.nsegs = L.nsegs;
+    prm.nblocks = (int32_t)nb;
+    prm.depth_last = (int32_t)(steps - (nb - 1) * D);
+    prm.debug_stall = debug_stall;
+    prm.sr_key = p->sr_key;
+    for (int k = 0; k < p->npts; ++k) {
+        prm.coef[k] = p->coef[k];
+        prm.coef_f[k] = (float)p->coef[k];
     }
-    for (int64_t k = 0; k < rem; ++k) {
-        const int64_t i = nb + k;
-        const void* src = (i == 0) ? src0 : stage_dst(i - 1);
-        e = naive_launch(p, src, stage_dst(i), nb * D + k + 1, st);
-        if (e != cudaSuccess) return fail_cuda(e);
-    }
+    int occ = 0;
+    e = rs3_occupancy(p, D, &occ);
+    if (e != cudaSuccess) return fail_cuda(e);
+    if (occ < 1) return EBISU_ERR_UNSUPPORTED;
+    int64_t grid = (int64_t)std::min(occ, q.ctas_per_sm) * dv.sms;
+    grid = std::min<int64_t>(grid, (prm.nitems + kRSWarps - 1) / kRSWarps);
+    e = rs3_launch(p, D, prm, (int)grid, st);
+    if (e != cudaSuccess) return fail_cuda(e);
     return EBISU_OK;
 }
 

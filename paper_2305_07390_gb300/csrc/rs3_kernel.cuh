@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(kRSThreads, RS3Geom<T, SHAPE, R>::minb())
         if (!__all_sync(FULL, ok)) return;
 
         // ---- geometry ----------------------------------------------------------
-        const bool dst_is_out = ((prm.nstages - 1 - blk) & 1) == 0;
+        const bool dst_is_out = ((prm.nblocks - 1 - blk) & 1) == 0;
         T* const dst = reinterpret_cast<T*>(dst_is_out ? prm.out : prm.ws);
         const T* const src = (blk == 0) ? reinterpret_cast<const T*>(prm.src0)
                                         : reinterpret_cast<const T*>(dst_is_out ? prm.ws : prm.out);

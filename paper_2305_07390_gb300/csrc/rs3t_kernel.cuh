@@ -23,9 +23,7 @@
 //  * Level-0 planes are staged 4 planes ahead in shared memory by per-lane
 //    cp.async (each lane copies and later reads back only its own cells).
 //  * Dirichlet pad cells keep their input value at every level (copied from
-//    the level below).
-//  * Every launch runs whole temporal blocks of depth t; the host runs the
-//    remaining steps % t steps with the one-step kernel.
+//    the level below); levels past the last block's depth pass values on.
 //  * Tiles (strip, band, z segment) of block b wait only for their 3 x 3 x 3
 //    neighbours of block b-1 (a tile's inputs reach t cells past its output,
 //    at most one patch, strip or segment away).
@@ -74,6 +72,21 @@ __device__ __forceinline__ void rs3t_cp_async(T* smem, const T* gmem, int src_si
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sa), "l"(gmem), "r"(src_size) : "memory");
 }
+
+// Step keys of a block's levels for stochastic rounding; empty otherwise.
+template <bool SR, int D>
+struct RS3TStepKeys {
+    __device__ __forceinline__ RS3TStepKeys(uint32_t, int) {}
+};
+template <int D>
+struct RS3TStepKeys<true, D> {
+    uint32_t k[D];
+    __device__ __forceinline__ RS3TStepKeys(uint32_t plan_key, int blk)
+    {
+#pragma unroll
+        for (int s = 1; s <= D; ++s) k[s - 1] = sr_step_key(plan_key, (uint32_t)(blk * D + s));
+    }
+};
 
 template <class T, int SHAPE, int D>
 __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
@@ -153,7 +166,9 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
         if (!__all_sync(FULL, ok)) return;
 
         // ---- geometry ----------------------------------------------------------
-        const bool dst_is_out = ((prm.nstages - 1 - blk) & 1) == 0;
+        const bool lastb = (blk == prm.nblocks - 1);
+        const int deff = lastb ? prm.depth_last : D;  // levels above deff pass values on
+        const bool dst_is_out = ((prm.nblocks - 1 - blk) & 1) == 0;
         T* const dst = reinterpret_cast<T*>(dst_is_out ? prm.out : prm.ws);
         const T* const src = (blk == 0) ? reinterpret_cast<const T*>(prm.src0)
                                         : reinterpret_cast<const T*>(dst_is_out ? prm.ws : prm.out);
@@ -201,12 +216,10 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
         // a lane's two columns as one copy (8 bytes FP32, 4 bytes BF16) when
         // both exist and every row starts them on a pair boundary (aligned
         // buffer, even row pitch -- hence even plane pitch -- and even column)
-        // stochastic rounding (BF16-SR storage): the step keys of this block's levels
-        uint32_t srk[Dt::kSR ? D : 1];
-        if constexpr (Dt::kSR) {
-#pragma unroll
-            for (int s = 1; s <= D; ++s) srk[s - 1] = sr_step_key(prm.sr_key, (uint32_t)(blk * D + s));
-        }
+        // stochastic rounding (BF16-SR storage): the step keys of this block's
+        // levels (an empty object for the other storage types, so that their
+        // code is exactly the plain form)
+        const RS3TStepKeys<Dt::kSR, D> srk(prm.sr_key, blk);
         constexpr int PB = 2 * (int)sizeof(T);  // bytes of a lane's column pair
         const bool pairs = !per && colok == 3u && ((ld1 & 1) == 0) && ((coloff[0] & 1) == 0) &&
                            ((reinterpret_cast<uintptr_t>(src) & (PB - 1)) == 0);
@@ -276,7 +289,7 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
                     const int sp_ = ((u - s - 1) % U + U) % U;  // slot of plane zs - 1
                     const int sn = ((u - s + 1) % U + U) % U;   // slot of plane zs + 1
                     const int ys = ya - (D - s);  // global row of level s's row 0
-                    const bool copy = !per && (zs < 0 || zs >= n0);
+                    const bool copy = (s > deff) || (!per && (zs < 0 || zs >= n0));
                     // x neighbours of level s-1 rows: WL = left lane's last
                     // column, WR = right lane's first column, per plane
                     // (0: zs-1, 1: zs, 2: zs+1) and row
@@ -332,19 +345,19 @@ __global__ void __launch_bounds__(kRSThreads, RS3TGeom<T, SHAPE, D>::minb())
                                 acc[v] = (k == 0) ? Dt::mul(ck, val) : Dt::fma(ck, val, acc[v]);
                             }
                         }
-                        // the cell's index in the stored array (stochastic rounding)
-                        uint32_t sr_row = 0;
-                        if constexpr (Dt::kSR) {
-                            const int zw = per ? ((zs < 0) ? zs + n0 : (zs >= n0 ? zs - n0 : zs)) : zs + pad;
-                            sr_row = (uint32_t)((int64_t)zw * lds) + (uint32_t)rowoff[i + s] + srk[s - 1];
-                        }
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
                             const bool keep = copy || prow || ((padc >> v) & 1u);
-                            C rd;
-                            if constexpr (Dt::kSR) rd = sr_round_bf16(acc[v], sr_row + (uint32_t)coloff[v]);
-                            else rd = Dt::widen(Dt::narrow(acc[v]));
-                            const C o = keep ? Q(s - 1, cs, ib, v) : rd;
+                            C o;
+                            if constexpr (Dt::kSR) {
+                                // the cell's index in the stored array picks its random bits
+                                const int zw = per ? ((zs < 0) ? zs + n0 : (zs >= n0 ? zs - n0 : zs)) : zs + pad;
+                                const uint32_t cell = (uint32_t)((int64_t)zw * lds) + (uint32_t)rowoff[i + s] +
+                                                      (uint32_t)coloff[v];
+                                o = keep ? Q(s - 1, cs, ib, v) : sr_round_bf16(acc[v], cell + srk.k[s - 1]);
+                            } else {
+                                o = keep ? Q(s - 1, cs, ib, v) : Dt::widen(Dt::narrow(acc[v]));
+                            }
                             if (s < D) {
                                 Q(s < D ? s : 0, cs, i, v) = o;
                             } else if (zs >= za && zs < zb && i < TY && ya + i < n1 && ((outc >> v) & 1u)) {

@@ -421,27 +421,16 @@ int ebisu_plan_tune_share(ebisu_plan_t plan, const void* in, void* out, int64_t 
     int rc = EBISU_OK;
     for (int i = 0; i < n; ++i) {
         plan->prm = cand[i];
-        // The 3D register-streaming build runs whole temporal blocks and ends
-        // a run with one-step launches for steps % depth steps: it is timed
-        // over whole blocks only (at least one), and every candidate is
-        // compared by its time per step scaled to `steps`, so that a short
-        // tuning run does not charge a depth for a tail that longer runs
-        // barely pay.
-        const int dq = cand[i].depth;
-        const int64_t st_i = (plan->ndim == 3 && cand[i].variant == 2 && dq > 1)
-                                 ? std::max<int64_t>(dq, steps - steps % dq)
-                                 : steps;
-        rc = ebisu_run(plan, in, out, st_i, workspace, stream);  // warm-up
+        rc = ebisu_run(plan, in, out, steps, workspace, stream);  // warm-up
         if (rc != EBISU_OK) break;
         cudaEventRecord(e0, st);
-        rc = ebisu_run(plan, in, out, st_i, workspace, stream);
+        rc = ebisu_run(plan, in, out, steps, workspace, stream);
         if (rc != EBISU_OK) break;
         cudaEventRecord(e1, st);
         rc = ebisu_sync(workspace, stream);
         if (rc != EBISU_OK) break;
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
-        ms = (float)((double)ms * (double)steps / (double)st_i);
         if (ms < best) {
             best = ms;
             bestp = cand[i];
