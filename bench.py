@@ -466,7 +466,10 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
     the oracle on the sampled grids small enough for it (whole grids), and
     optionally the same grids are timed one launch each.  Each bucket is
     tuned with its share of the GPU inside the batch (its grid's cells over
-    the batch's cells), so the streamed bands stay tall."""
+    the batch's cells), so the streamed bands stay tall; the batch is then
+    timed with those parameters and with the cost model's defaults, and the
+    faster set is kept (a bucket's tuning run has its grid alone on the GPU,
+    which need not rank candidates as the batch does)."""
     import numpy as np
     import torch
     from paper_2305_07390_gb300 import ebisu, synth
@@ -475,7 +478,8 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
     updates = int(sum(a * b * s for a, b, s in mix))
     out = {"workload": f"batch: {count} uneven 2D 9-point box grids (sides log-uniform in [256, 4096], aspect "
                        "[0.25, 4]), 16-512 steps each, Dirichlet, one persistent launch per storage form; tiles "
-                       "and depth from the autotuner per shape bucket", "n_grids": len(mix), "cells": cells,
+                       "and depth from the autotuner per shape bucket or the cost model, whichever batch runs "
+                       "faster", "n_grids": len(mix), "cells": cells,
            "cell_updates": updates, "by_form": {}}
     # the grids the oracle checks: the smallest ones, whole
     order = sorted(range(len(mix)), key=lambda i: mix[i][0] * mix[i][1])
@@ -497,8 +501,27 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
     problems = [synth.problem(2, (ny, nx), synth.BOX, 1, synth.DIRICHLET, seed=synth.DEFAULT_SEED + i)
                 for i, (ny, nx, _) in enumerate(mix)]
     out["generate_s"] = time.perf_counter() - t0
+    def time_batch(plans, xs, ys, steps_l):
+        ws = torch.empty(ebisu.batch_workspace_bytes(plans, steps_l), dtype=torch.uint8, device="cuda")
+        b = ebisu.Batch(plans, xs, ys, steps_l, ws)
+        for _ in range(warmup):
+            b.launch()
+        torch.cuda.synchronize()
+        assert b.sync() == 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            b.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert b.sync() == 0
+        kernels = sorted({"rs_kernel" if (p.params().variant == 2 or p.params().fused_variant == 2)
+                          else "tb_kernel" for p in plans})
+        del b, ws
+        return e0.elapsed_time(e1) / steps, kernels
+
     for fname, dt, rounding in BATCH_FORMS:
-        plans, xs, ys, steps_l = [], [], [], []
+        plans, xs, ys, steps_l, defaults = [], [], [], [], []
         tuned = {}
         t0 = time.perf_counter()
         for i, (ny, nx, st) in enumerate(mix):
@@ -506,6 +529,7 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
             plan = ebisu.Plan(2, (ny, nx), ebisu.BOX, 1, c, dt, ebisu.DIRICHLET)
             if rounding == "sr":
                 plan.set_rounding(ebisu.ROUND_STOCHASTIC, synth.DEFAULT_SEED)
+            defaults.append(plan.params())  # the cost model's pick for this grid
             x = torch.from_numpy(g).to(ebisu.torch_dtype(dt)).cuda()
             y = torch.empty_like(x)
             key = (round(2 * math.log2(ny)), round(2 * math.log2(nx)))
@@ -527,25 +551,26 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
             ys.append(y)
             steps_l.append(st)
         t_tune = time.perf_counter() - t0
-        ws = torch.empty(ebisu.batch_workspace_bytes(plans, steps_l), dtype=torch.uint8, device="cuda")
-        b = ebisu.Batch(plans, xs, ys, steps_l, ws)
-        for _ in range(warmup):
-            b.launch()
-        torch.cuda.synchronize()
-        assert b.sync() == 0
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            b.launch()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        assert b.sync() == 0
-        ms_batch = e0.elapsed_time(e1) / steps
+        # Each bucket was tuned on one grid running alone, which need not
+        # predict the grid inside the batch, so the batch itself decides: it
+        # is timed with the tuned parameters and with the cost model's, and
+        # keeps the faster (results are identical either way).
+        ms_tuned, k_tuned = time_batch(plans, xs, ys, steps_l)
+        tuned_params = [p.params() for p in plans]
+        for p, q in zip(plans, defaults):
+            apply_params(ebisu, p, q)
+        ms_def, k_def = time_batch(plans, xs, ys, steps_l)
+        use_tuned = ms_tuned <= ms_def
+        if use_tuned:
+            for p, q in zip(plans, tuned_params):
+                apply_params(ebisu, p, q)
+        ms_batch = min(ms_tuned, ms_def)
         row = {"ms_batched": ms_batch, "cell_updates_per_s": updates / (ms_batch * 1e-3),
                "rounding": "stochastic" if rounding == "sr" else "nearest even",
+               "params": "tuned per shape bucket" if use_tuned else "cost-model defaults",
+               "ms_tuned_per_bucket": ms_tuned, "ms_cost_model_defaults": ms_def,
                "buckets_tuned": len(tuned), "tuning_s": t_tune,
-               "kernels": sorted({"rs_kernel" if (p.params().variant == 2 or p.params().fused_variant == 2)
-                                  else "tb_kernel" for p in plans})}
+               "kernels": k_tuned if use_tuned else k_def}
         if check:
             errs = []
             for i in sample:
@@ -561,6 +586,7 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
         if one_by_one:
             big = max(p.workspace_bytes() for p in plans)
             wsa = torch.empty(big, dtype=torch.uint8, device="cuda")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for p, x, y, st in zip(plans, xs, ys, steps_l):
                 p.run(x, y, st, wsa)
@@ -570,7 +596,7 @@ def batch_leg(warmup, steps, count=512, check=True, one_by_one=False):
             row["batching_speedup"] = row["ms_one_by_one"] / ms_batch
             del wsa
         out["by_form"][fname] = row
-        del plans, xs, ys, ws, b
+        del plans, xs, ys
         torch.cuda.empty_cache()
     f64 = out["by_form"]["f64"]["ms_batched"]
     for fname, _, _ in BATCH_FORMS[1:]:
