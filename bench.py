@@ -300,6 +300,86 @@ def run_set3d(args):
     print(json.dumps({"workload": f"3D FP64 stencil set, {n}^3, {steps} steps", "rows": rows}), flush=True)
 
 
+def run_slab(args):
+    """Slab decomposition of one grid (paper_2305_07390_gb300/slab.py) on one
+    GPU: the FP32 5-point star on 8192^2 for 1000 steps, cut into 2 or 4
+    slabs along y, each slab stepped by its own plan for k steps between
+    ghost exchanges (device-to-device copies of g = r*k + r rows per side),
+    against one run over the whole grid.  The slabs run one after another
+    on the one GPU, so this measures what the decomposition itself costs
+    (ghost rows recomputed, shorter launches, the copies), not a multi-GPU
+    speedup.  Every decomposed result is checked equal to the whole-grid
+    result."""
+    import torch
+    from paper_2305_07390_gb300 import ebisu, slab, synth
+    n, steps, r = 8192, 1000, 1
+    dims = (n, n)
+    g, c = synth.problem(2, dims, ebisu.STAR, r, synth.DIRICHLET, seed=synth.DEFAULT_SEED)
+    x = torch.from_numpy(g).float().cuda()
+    del g
+    stream = torch.cuda.current_stream()
+    sh = ebisu.current_stream_handle()
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    whole = ebisu.Plan(2, dims, ebisu.STAR, r, c, ebisu.F32, ebisu.DIRICHLET)
+    ws = whole.workspace()
+    ref = torch.empty_like(x)
+    whole.tune(x, ref, 96, ws, max_candidates=args.tune)
+    ms_whole = timed(lambda: whole.run(x, ref, steps, ws, stream=sh))
+    assert whole.sync(ws) == 0
+    rows = [{"slabs": 1, "exchange_every": steps, "ms": ms_whole,
+             "cell_updates_per_s": n * n * steps / (ms_whole * 1e-3), "params": whole.params().as_dict()}]
+    print(json.dumps(rows[-1]), flush=True)
+    q = whole.params()
+    for world in (2, 4):
+        for k in (16, 64, 250):
+            geos = slab.geometries(n, r, k, world)
+            plans, wss, locs, outs = [], [], [], []
+            for geo in geos:
+                p = ebisu.Plan(2, (geo.local_interior, n), ebisu.STAR, r, c, ebisu.F32, ebisu.DIRICHLET)
+                apply_params(ebisu, p, q)
+                plans.append(p)
+                wss.append(p.workspace())
+                locs.append(slab.scatter(x, geo))
+                outs.append(torch.empty_like(locs[-1]))
+            init = [t.clone() for t in locs]
+
+            def solve():
+                for i in range(world):
+                    locs[i].copy_(init[i])
+
+                def step(t):
+                    for i in range(world):
+                        slab.device_step(plans[i], locs[i], outs[i], wss[i], t, stream=sh)
+                        locs[i], outs[i] = outs[i], locs[i]
+
+                slab.run_blocks(steps, k, step, lambda: slab.LocalExchange().exchange(geos, locs))
+
+            ms = timed(solve)
+            for p, w in zip(plans, wss):
+                assert p.sync(w) == 0
+            got = torch.full_like(x, float("nan"))
+            for geo, loc in zip(geos, locs):
+                slab.gather_into(got, loc, geo)
+            rows.append({"slabs": world, "exchange_every": k, "ghost_rows": geos[0].ghost, "ms": ms,
+                         "cell_updates_per_s": n * n * steps / (ms * 1e-3),
+                         "of_whole_grid": ms_whole / ms, "equal_to_whole_grid": bool(torch.equal(got, ref))})
+            print(json.dumps(rows[-1]), flush=True)
+            del plans, wss, locs, outs, init, got
+            torch.cuda.empty_cache()
+    print(json.dumps({"workload": f"slab decomposition on one GPU: FP32 5-point star, {n}^2, {steps} steps",
+                      "rows": rows}), flush=True)
+
+
 def run_paper_sizes(args):
     """The paper's own benchmark stencils at its domain sizes (Table 2): the
     2D j2d5pt (8352^2), j2d9pt (9-point star, 8064^2), j2d9pt-gol (9-point
@@ -773,11 +853,13 @@ def main():
     ap.add_argument("--naive", action="store_true", help="--case: the one-step-per-launch kernel")
     ap.add_argument("--repeat", type=int, default=0, help="--case: time this many further solves")
     ap.add_argument("--ablate", type=int, default=0, help="--case: ablation mask of the shared-memory build")
-    ap.add_argument("--workload", default="set", choices=["set", "set3d", "batch", "serve", "paper", "ablation"],
+    ap.add_argument("--workload", default="set",
+                    choices=["set", "set3d", "batch", "serve", "paper", "ablation", "slab"],
                     help="set: the FP64 2D stencil set (default, the headline line); set3d: the FP64 3D "
                          "set; batch: 512 uneven 2D 9-point box grids in one persistent launch per dtype; "
                          "serve: Poisson arrivals through the serving loop; paper: the paper's stencils at "
-                         "its domain sizes; ablation: what each design element buys")
+                         "its domain sizes; ablation: what each design element buys; slab: one grid cut "
+                         "into slabs with ghost exchanges, on one GPU")
     ap.add_argument("--serve-rates", default="5,10,20,50,100,200,500,1000,2000")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
@@ -793,6 +875,8 @@ def main():
         return run_ablation(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "slab":
+        return run_slab(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
