@@ -170,3 +170,63 @@ def test_3d_fullsize_blocked_equals_naive(shape, r):
     plan.run(x, yn, steps, ws, naive=True)
     assert plan.sync(ws) == 0
     assert torch.equal(y, yn), f"params {plan.params().as_dict()}"
+
+
+# ---- grids of more than 2^31 stored cells -----------------------------------
+# Every element offset past 2^31 needs 64-bit index arithmetic.  The grid is
+# generated row block by row block from the seeded stream (counter-based, so
+# any row range can be drawn on its own) straight into device memory; the
+# oracle's corner cones are drawn the same way.
+
+def _rows(dims_stored, seed, r0, r1):
+    """Stored rows (first axis) r0 .. r1-1 of the seeded grid, FP64."""
+    inner = int(np.prod(dims_stored[1:]))
+    v = synth.uniform01(seed, r0 * inner, (r1 - r0) * inner)
+    return v.reshape((r1 - r0,) + tuple(dims_stored[1:]))
+
+
+@pytest.mark.parametrize("ndim,dims,rs", [
+    (2, (46341, 46341), dict(variant=2, depth=8, tile_s=2048, ctas_per_sm=3)),
+    (3, (1292, 1292, 1292), dict(variant=2, depth=3, tile_s=0, ctas_per_sm=2))])
+def test_more_than_2_to_31_cells(ndim, dims, rs):
+    eb = _eb()
+    r, shape, steps, seed = 1, 0, 3, 97
+    st = synth.stored_shape(dims, r, synth.DIRICHLET)
+    assert int(np.prod(st)) > 2 ** 31
+    c = synth.coefficients(ndim, shape, r, dims, synth.DIRICHLET, seed)
+    x = torch.empty(st, dtype=torch.float32, device="cuda")
+    blk = 1024 if ndim == 2 else 64
+    for a in range(0, st[0], blk):
+        b = min(st[0], a + blk)
+        x[a:b] = torch.from_numpy(_rows(st, seed, a, b)).float().cuda()
+    plan = eb.Plan(ndim, dims, shape, r, c, eb.F32, eb.DIRICHLET)
+    ws = plan.workspace()
+    out = {}
+    tb = (dict(variant=0, tile_x=64, tile_s=32, depth=3, ctas_per_sm=2) if ndim == 2 else
+          dict(variant=0, tile_x=32, tile_y=8, tile_s=16, depth=2, ctas_per_sm=2))
+    for name, params, kw in [("naive", None, {"naive": True}), ("shared", tb, {}), ("rs", rs, {})]:
+        if params is not None:
+            plan.set_params(**params)
+        y = torch.empty_like(x)
+        plan.run(x, y, steps, ws, **kw)
+        assert plan.sync(ws) == 0, name
+        out[name] = y
+        if name != "naive":
+            assert torch.equal(y, out["naive"]), f"{name} differs from the one-step kernel"
+            del out[name], y
+    y = out["naive"]
+    # oracle cones of the first and the last corner window (the last one's
+    # offsets lie past 2^31)
+    w = 6
+    span = w + 2 * r + steps * r
+    ch = c.astype(np.float32).astype(np.float64)
+    for high in (False, True):
+        r0 = st[0] - span if high else 0
+        cut_rows = _rows(st, seed, r0, r0 + span).astype(np.float32).astype(np.float64)
+        sl = tuple(slice(s - span, s) if high else slice(0, span) for s in st[1:])
+        cut = np.ascontiguousarray(cut_rows[(slice(None),) + sl])
+        ref = oracle.run(cut, shape, r, ch, synth.DIRICHLET, steps)
+        win = tuple(slice(span - r - w, span - r) if high else slice(r, r + w) for _ in range(ndim))
+        dev = y[(slice(r0, r0 + span),) + sl].double().cpu().numpy()[win]
+        err = float(np.max(np.abs(dev - ref[win])) / np.max(np.abs(ref[win])))
+        assert err <= 1e-5, f"corner {'high' if high else 'low'}: {err}"
