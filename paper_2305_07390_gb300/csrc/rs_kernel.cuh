@@ -347,14 +347,25 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                     // an odd-sized array's last element, whose pair would end
                     // past the array, is copied alone
                     const int64_t a = elem0(y) & ~(int64_t)1;
+                    if (!G && !per) {
+                        // a Dirichlet tile off the general path loads
+                        // interior rows only and every lane's columns lie
+                        // inside the padded row, so its pairs start at
+                        // (y+pad)*lds - 1 >= 0 and end at most one element
+                        // into the next stored row: every pair is inside the
+                        // array
 #pragma unroll
-                    for (int q = 0; q < SW; q += 2) {
-                        const int64_t e = a + q;
-                        const bool ok = e >= 0 && e + 1 < total;
-                        if (!ok && e >= 0 && e < total) {
-                            sp[q] = Dt::raw(src + e);
-                        } else {
-                            rs_cp_async<4>(sp + q, ok ? src + e : src, ok ? 4 : 0);
+                        for (int q = 0; q < SW; q += 2) rs_cp_async<4>(sp + q, src + (a + q), 4);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < SW; q += 2) {
+                            const int64_t e = a + q;
+                            const bool ok = e >= 0 && e + 1 < total;
+                            if (!ok && e >= 0 && e < total) {
+                                sp[q] = Dt::raw(src + e);
+                            } else {
+                                rs_cp_async<4>(sp + q, ok ? src + e : src, ok ? 4 : 0);
+                            }
                         }
                     }
                 }
