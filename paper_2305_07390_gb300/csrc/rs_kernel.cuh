@@ -287,6 +287,17 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                       (!per && (ya - R * D < 0 || yb + R * D > n0i));
         }
 
+        // 2-byte storage: every pair copy of this tile lies inside the array
+        // when the tile is Dirichlet, loads interior rows only and every
+        // lane's columns lie inside the padded row (the copies then start at
+        // (y+pad)*lds - 1 >= 0 and end at most one element into the next
+        // stored row), so its copies need no bounds checks
+        bool stage_in = false;
+        if constexpr (sizeof(T) == 2) {
+            stage_in = !per && !__any_sync(FULL, lvm != (1u << RW) - 1u) && ya - R * D >= 0 &&
+                       yb + R * D <= n0i;
+        }
+
         // level-0 row y (general loop: rows past the loaded region are
         // prefetched for the ramp-down steps and never used, so skipped)
         auto load_row = [&](C(&v)[RW], int y) {
@@ -347,13 +358,10 @@ __global__ void __launch_bounds__(kRSThreads, RSGeom<T, SHAPE, R>::minb(D, BATCH
                     // an odd-sized array's last element, whose pair would end
                     // past the array, is copied alone
                     const int64_t a = elem0(y) & ~(int64_t)1;
-                    if (!G && !per) {
-                        // a Dirichlet tile off the general path loads
-                        // interior rows only and every lane's columns lie
-                        // inside the padded row, so its pairs start at
-                        // (y+pad)*lds - 1 >= 0 and end at most one element
-                        // into the next stored row: every pair is inside the
-                        // array
+                    // (the lean loop's interior tiles, !G, have the
+                    // property by construction; the general loop tests it
+                    // per tile)
+                    if ((!G && !per) || (!lean && stage_in)) {
 #pragma unroll
                         for (int q = 0; q < SW; q += 2) rs_cp_async<4>(sp + q, src + (a + q), 4);
                     } else {
